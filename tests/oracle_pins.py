@@ -1,0 +1,208 @@
+"""Checks that pin the CPU oracle to facts fixed outside itself.
+
+Each check raises AssertionError on failure.  They are collected by
+test_oracle_pins.py and re-run against deliberately broken builds of the
+oracle in test_oracle_mutants.py, which asserts that every plausible mistake
+(a dropped term, a wrong sign or index, an off-by-one) fails at least one.
+
+Sources of truth, none of them the oracle itself:
+  - hand_placed: separations known by construction (golden/hand_placed.txt);
+  - totals: n(n-1)/2 auto pairs and n_a n_b cross pairs (Sec. 2);
+  - dr_rd: the cross count is symmetric in its arguments;
+  - d_equals_r: random catalogue == data gives w = 2/n exactly (Eq. 2 with
+    pair totals; derivation in the check);
+  - r_is_d_twice: random catalogue == data listed twice gives
+    w = (3n - 2) / (2n(n - 1));
+  - cross_identity: R1 == D1 gives the cross estimator w = 0;
+  - analytic_rr: uniform full-sky pairs fall in [t1, t2) with probability
+    (cos t1 - cos t2)/2, and the bin counts have binomial variance;
+  - bruteforce_angles: App. A's formula (with atan2) in long double on small
+    random catalogues agrees with the oracle's slots;
+  - edges_*: the three binning modes of Sec. 2.1;
+  - chord_values: chord lengths of 60, 90 and 180 degrees.
+"""
+from __future__ import annotations
+
+import bisect
+import math
+import os
+
+import numpy as np
+
+from oracle import oracle as O
+from paper_1208_3658_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+ARCMIN = 1.0 / 60.0
+
+GOLDEN_EDGES = {
+    "log16_1am_5d": (1.0 * ARCMIN, 5.0, 16, O.LN),
+    "log32_halfam_20d": (0.5 * ARCMIN, 20.0, 32, O.LN),
+    "lin12_0_180": (0.0, 180.0, 12, O.LINEAR),
+}
+
+
+def _slot_by_angle(edges_deg, theta_deg):
+    """Expected slot from the angle itself: number of edges <= theta."""
+    return bisect.bisect_right(list(edges_deg), theta_deg)
+
+
+def check_hand_placed():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "hand_placed.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) > 100
+    for name, (lo, hi, K, mode) in GOLDEN_EDGES.items():
+        e = O.edges(lo, hi, K, mode)
+        sel = [r for r in rows if r[0] == name]
+        a = np.array([[float(r[1]), float(r[2])] for r in sel]).reshape(-1)
+        b = np.array([[float(r[3]), float(r[4])] for r in sel]).reshape(-1)
+        A, B = O.radec_to_xyz(a), O.radec_to_xyz(b)
+        for i, r in enumerate(sel):
+            got = O.count_xyz(A[:, i:i + 1], B[:, i:i + 1], e, False)
+            want = np.zeros(K + 2, np.uint64)
+            want[_slot_by_angle(e, float(r[5]))] = 1
+            assert np.array_equal(got, want), (name, r, got)
+
+
+def _patch_cat(n, seed, path):
+    return synth.uniform(synth.Patch(0.0, 10.0, 0.0, 10.0), n, seed, "test", path)
+
+
+def check_totals():
+    e = O.edges(1.0 * ARCMIN, 5.0, 16)
+    for n_a, n_b in [(0, 0), (1, 0), (1, 1), (2, 3), (31, 33), (257, 100)]:
+        A = _patch_cat(n_a, 3, n_a)
+        B = _patch_cat(n_b, 4, n_b)
+        auto = O.count(A, None, e, True)
+        cross = O.count(A, B, e, False)
+        assert int(auto.sum()) == n_a * (n_a - 1) // 2, (n_a, auto)
+        assert int(cross.sum()) == n_a * n_b, (n_a, n_b, cross)
+
+
+def check_dr_rd():
+    e = O.edges(1.0 * ARCMIN, 5.0, 16)
+    A, B = _patch_cat(700, 5, 1), _patch_cat(500, 6, 2)
+    assert np.array_equal(O.count(A, B, e, False), O.count(B, A, e, False))
+
+
+def _clustered(n, seed):
+    fp = synth.Patch(0.0, 5.0, 0.0, 5.0)
+    return synth.clustered(fp, n, max(1, n // 50), 3.0, seed, "test", "data")
+
+
+def check_d_equals_r():
+    """R = D: DR counts ordered pairs, the n self pairs landing in underflow
+    (e_0 > 0), so DR_k = 2 DD_k and RR_k = DD_k for k >= 1.  With the pair
+    totals, w_k = [2DD/(n(n-1)) - 2*2DD/n^2 + 2DD/(n(n-1))] / [2DD/(n(n-1))]
+    = 2 - 2(n-1)/n = 2/n for every bin with DD_k > 0."""
+    n = 800
+    e = O.edges(1.0 * ARCMIN, 5.0, 16)
+    D = _clustered(n, 7)
+    DD = O.count(D, None, e, True)
+    DR = O.count(D, D, e, False)
+    w = O.ls(DD, DR, DD, n, n)
+    nz = DD[1:-1] > 0
+    assert nz.sum() >= 10
+    assert np.all(np.abs(w[nz] - 2.0 / n) <= 1e-12 * 3.0), w[nz]
+
+
+def check_r_is_d_twice():
+    """R = D listed twice (n_r = 2n): for k >= 1, with P_k = DD_k,
+    DR_k = 4 P_k, RR_k = 4 P_k (pairs within each copy plus ordered pairs
+    across copies), N_DD = n(n-1)/2, N_DR = 2n^2, N_RR = n(2n-1), so
+    w_k = (3n - 2) / (2n(n - 1))."""
+    n = 600
+    e = O.edges(1.0 * ARCMIN, 5.0, 16)
+    D = _clustered(n, 8)
+    R = np.concatenate([D, D])
+    DD = O.count(D, None, e, True)
+    DR = O.count(D, R, e, False)
+    RR = O.count(R, None, e, True)
+    w = O.ls(DD, DR, RR, n, 2 * n)
+    nz = DD[1:-1] > 0
+    want = (3 * n - 2) / (2 * n * (n - 1))
+    assert nz.sum() >= 10
+    assert np.all(np.abs(w[nz] - want) <= 1e-12 * 3.0), (w[nz], want)
+
+
+def check_cross_identity():
+    """Cross estimator with R1 = D1: d1d2 - d1r2 - r1d2 + r1r2 = 0."""
+    e = O.edges(1.0 * ARCMIN, 5.0, 16)
+    D1, D2 = _clustered(400, 9), _clustered(500, 10)
+    R2 = _patch_cat(450, 11, 3)
+    D1D2 = O.count(D1, D2, e, False)
+    D1R2 = O.count(D1, R2, e, False)
+    w = O.ls_cross(D1D2, D1R2, D1D2, D1R2, 400, 500, 400, 450)
+    ok = D1R2[1:-1] > 0
+    assert ok.sum() >= 10
+    assert np.all(np.abs(w[ok]) <= 1e-12 * 4.0), w[ok]
+
+
+def check_analytic_rr(n: int = 20_000):
+    """Uniform full-sky points: a pair falls in [t1, t2) with probability
+    p = (cos t1 - cos t2)/2; indicators of pairs sharing a point are
+    uncorrelated (isotropy), so Var(RR_k) = N p (1 - p) exactly."""
+    e = O.edges(1.0, 120.0, 16)
+    R = synth.uniform(synth.FullSky(), n, 12, "test", "random")
+    RR = O.count(R, None, e, True).astype(np.float64)
+    N = n * (n - 1) / 2
+    cosd = np.cos(np.radians(np.concatenate([[0.0], e, [180.0]])))
+    p = (cosd[:-1] - cosd[1:]) / 2.0
+    sigma = np.sqrt(N * p * (1 - p))
+    z = (RR - N * p) / sigma
+    assert np.all(np.abs(z) <= 5.0), z
+
+
+def check_bruteforce_angles(n: int = 400):
+    """App. A: theta = atan2(sqrt(A + B^2), C) in long double (atan2 for
+    theta > 90 deg), binned by degree edges, against the oracle's slots for
+    every pair of a small catalogue pair mixing a patch and the full sky."""
+    e = O.edges(0.5 * ARCMIN, 100.0, 24)
+    a = np.concatenate([_clustered(n // 2, 13),
+                        synth.uniform(synth.FullSky(), n // 2, 14, "test", "random")])
+    b = np.concatenate([_patch_cat(n // 2, 15, 4),
+                        synth.uniform(synth.FullSky(), n // 2, 16, "test", "random")])
+    L = np.longdouble
+    ra1 = a[0::2].astype(L)[:, None] * (L(np.pi) / 180)
+    de1 = a[1::2].astype(L)[:, None] * (L(np.pi) / 180)
+    ra2 = b[0::2].astype(L)[None, :] * (L(np.pi) / 180)
+    de2 = b[1::2].astype(L)[None, :] * (L(np.pi) / 180)
+    da = ra2 - ra1
+    Aq = np.cos(de2) ** 2 * np.sin(da) ** 2
+    Bq = np.cos(de1) * np.sin(de2) - np.sin(de1) * np.cos(de2) * np.cos(da)
+    Cq = np.sin(de1) * np.sin(de2) + np.cos(de1) * np.cos(de2) * np.cos(da)
+    theta = np.arctan2(np.sqrt(Aq + Bq * Bq), Cq) * (L(180) / L(np.pi))
+    slots = np.searchsorted(e.astype(L), theta.reshape(-1), side="right")
+    want = np.bincount(slots, minlength=len(e) + 1).astype(np.uint64)
+    got = O.count(a, b, e, False)
+    assert np.array_equal(got, want), (got, want)
+
+
+def check_edges_modes():
+    lo, hi, K = 1.0 * ARCMIN, 5.0, 16
+    for mode in (O.LN, O.LOG10):
+        e = O.edges(lo, hi, K, mode)
+        assert e[0] == lo and e[-1] == hi
+        r = e[1:] / e[:-1]
+        assert np.allclose(r, (hi / lo) ** (1.0 / K), rtol=1e-13, atol=0), r
+    for lo_l, hi_l in [(0.0, 3.0), (1.0, 4.0)]:
+        e = O.edges(lo_l, hi_l, 12, O.LINEAR)
+        assert np.allclose(np.diff(e), 0.25, rtol=1e-13, atol=0)
+        assert e[0] == lo_l and e[-1] == hi_l
+
+
+def check_chord_values():
+    c = O.chord2(np.array([0.0, 60.0, 90.0, 180.0]))
+    assert c[0] == 0.0
+    assert abs(c[1] - 1.0) <= 4e-16 and abs(c[2] - 2.0) <= 8e-16 and abs(c[3] - 4.0) <= 8e-16
+    t = 1e-3  # degrees: small-angle chord^2 ~ (t in radians)^2 (1 - t^2/12)
+    cs = O.chord2(np.array([t]))[0]
+    tr = math.radians(t)
+    assert abs(cs - tr * tr * (1 - tr * tr / 12)) <= 1e-15 * cs
+
+
+ALL_CHECKS = [
+    check_hand_placed, check_totals, check_dr_rd, check_d_equals_r,
+    check_r_is_d_twice, check_cross_identity, check_analytic_rr,
+    check_bruteforce_angles, check_edges_modes, check_chord_values,
+]
