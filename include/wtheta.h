@@ -1,0 +1,217 @@
+/*
+ * wtheta.h -- C ABI of libwtheta: exact angular pair counts (DD, DR, RR) and
+ * the Landy-Szalay estimate of the two-point angular correlation function
+ * w(theta), on one NVIDIA GB300 (sm_103a).
+ *
+ * The computation is the one stated in Sec. 2 of "Cosmological calculations
+ * on the GPU" (Bard, Bellis, Allen, Yepremyan, Kratochvil; arXiv:1208.3658):
+ * for every pair of galaxies, the angular separation (App. A) is binned into
+ * a histogram between user-set limits (Sec. 2.1); DD and RR count each
+ * unordered pair of one catalogue once, with no self pairs (n(n-1)/2 pairs),
+ * DR counts every data-random pair (n n_r pairs), and Eq. 2 combines them.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: WTHETA_OK (0) or a negative WTHETA_E* code.  Nothing is
+ *    written to outputs when a call fails argument validation.
+ *  - Angles are FP64 degrees.  Catalogues are interleaved FP64
+ *    [ra_0, dec_0, ra_1, dec_1, ...], RA any finite value, |Dec| <= 90.
+ *  - Bin edges e_0 < e_1 < ... < e_K (K = n_bins, 1 <= K <= 256) are FP64
+ *    degrees in [0, 180], host memory.  A pair with separation theta lands in
+ *    slot 0 (underflow) if theta < e_0, slot k (1..K) if
+ *    e_{k-1} <= theta < e_k, slot K+1 (overflow) if theta >= e_K.  The
+ *    comparison is made exactly on the squared chord
+ *    s = |a - b|^2 of the FP64 unit vectors, evaluated
+ *    ((dx*dx + dy*dy) + dz*dz) with IEEE round-to-nearest and no fused
+ *    operations, against c_k = 4 sin^2(e_k pi / 360) computed on the host.
+ *    Counts are exact for that predicate.
+ *  - Count arrays have K+2 uint64 slots (underflow, bins 1..K, overflow).
+ *  - Device pointers are borrowed: the library never frees them, and they
+ *    must be on the device that is current when the call is made.
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Device outputs are written asynchronously on it; the caller
+ *    synchronises before reading them.  Scratch memory is taken from the
+ *    device's stream-ordered pool on the same stream and returned on it.
+ *  - Problems only the device can see (non-finite coordinates, |Dec| > 90,
+ *    non-unit vectors) set bits in a sticky per-device error word, read and
+ *    cleared by wtheta_get_error().  The counts of such a call are undefined.
+ */
+#ifndef WTHETA_H
+#define WTHETA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define WTHETA_OK 0
+#define WTHETA_EINVAL (-1)   /* bad size, pointer, edge array or option      */
+#define WTHETA_ENOMEM (-2)   /* device or host allocation failed             */
+#define WTHETA_ECUDA (-3)    /* a CUDA runtime call failed                   */
+#define WTHETA_ETIMEOUT (-4) /* a bounded device or host wait gave up        */
+#define WTHETA_EBUDGET (-5)  /* a request does not fit the memory budget     */
+#define WTHETA_EDEVICE (-6)  /* the device error word is non-zero            */
+
+/* bits of the device error word (wtheta_get_error) */
+#define WTHETA_DERR_NONFINITE 1u  /* an input coordinate is NaN or infinite  */
+#define WTHETA_DERR_DEC_RANGE 2u  /* |Dec| > 90 degrees                      */
+#define WTHETA_DERR_NOT_UNIT 4u   /* an xyz input is not a unit vector       */
+
+/* ---- binning modes (Sec. 2.1: evenly spaced, natural-log, base-10 log) -- */
+#define WTHETA_BINS_LINEAR 0
+#define WTHETA_BINS_LN 1
+#define WTHETA_BINS_LOG10 2
+
+/* Message for a status code (static string, never NULL). */
+const char* wtheta_strerror(int status);
+
+/*
+ * Bin edges for the three binning modes of Sec. 2.1 (user-set low and high
+ * limits; evenly spaced, logarithmic or base-10 logarithmic widths).
+ *   LINEAR: e_k = lo + k (hi - lo)/K
+ *   LN:     e_k = lo exp(k ln(hi/lo)/K)
+ *   LOG10:  e_k = lo 10^(k log10(hi/lo)/K)
+ * with e_0 = lo and e_K = hi exactly.  The two logarithmic modes give the
+ * same geometric edges up to rounding; the base names how the width is stated.
+ * lo_deg >= 0 (> 0 for the log modes), hi_deg in (lo_deg, 180].
+ * edges_out: host, K+1 doubles, written.  EINVAL on bad limits or K.
+ */
+int wtheta_edges(double lo_deg, double hi_deg, int32_t n_bins, int32_t mode,
+                 double* edges_out);
+
+/*
+ * Squared-chord edges c_k = 4 sin^2(e_k pi/360) (App. A geometry: the chord
+ * between unit vectors at angle theta is 2 sin(theta/2)).  These are the FP64
+ * thresholds every count compares against.  Host in, host out (K+1 doubles).
+ * EINVAL if the edges are not strictly increasing within [0, 180].
+ */
+int wtheta_chord2_edges(const double* edges_deg, int32_t n_bins, double* c_out);
+
+/*
+ * The FP32 screening thresholds the counting kernel uses (host only; exposed
+ * so the guard band can be tested).  For each edge k, [lo_bits[k], hi_bits[k]]
+ * is an interval of FP32 bit patterns (non-negative floats order like their
+ * bits) around the FP32 edge: an FP32 squared chord below lo_bits[k] is
+ * certainly below c_k in FP64 and one above hi_bits[k] certainly at or above
+ * it; anything inside is recomputed in FP64.  The half-width bounds the
+ * rounding of the unit vectors to FP32 and of the FP32 evaluation
+ * d = a - b, s = fma(dz, dz, fma(dy, dy, dx*dx)).  All outputs host, K+1.
+ */
+int wtheta_guard_band(const double* edges_deg, int32_t n_bins, uint32_t* lo_bits,
+                      uint32_t* hi_bits, double* half_width);
+
+/*
+ * Exact pair counts between two catalogues (Sec. 2): the DD/RR auto count or
+ * the DR cross count, on the GPU.
+ *   ra_dec_a, ra_dec_b: device, interleaved FP64 degrees, n_a / n_b points.
+ *   is_auto = 1: ra_dec_b must be NULL or equal to ra_dec_a, n_b == n_a or 0;
+ *     every unordered pair i < j of catalogue a is counted once, no self
+ *     pairs: the slots sum to n_a (n_a - 1) / 2.
+ *   is_auto = 0: all n_a n_b ordered pairs (i in a, j in b): the slots sum to
+ *     n_a n_b.  Coincident points (theta = 0) are pairs like any other.
+ *   bin_edges_deg: host, K+1 doubles (see the conventions above).
+ *   counts: device, K+2 uint64, overwritten.
+ * RA/Dec are converted to FP64 unit vectors on the device (CUDA's sin/cos,
+ * which may differ from a host libm in the last place).  n = 0 gives all-zero
+ * counts.  EINVAL on bad arguments, ENOMEM, ECUDA.
+ */
+int wtheta_count(const double* ra_dec_a, int64_t n_a, const double* ra_dec_b,
+                 int64_t n_b, const double* bin_edges_deg, int32_t n_bins,
+                 int32_t is_auto, uint64_t* counts, void* stream);
+
+/*
+ * As wtheta_count, from caller-supplied FP64 unit vectors instead of RA/Dec.
+ *   xyz_a, xyz_b: device, SoA: x[0..n), y[0..n), z[0..n) (3n doubles).
+ * Counts are a pure function of these bits and the edges.
+ */
+int wtheta_count_xyz(const double* xyz_a, int64_t n_a, const double* xyz_b,
+                     int64_t n_b, const double* bin_edges_deg, int32_t n_bins,
+                     int32_t is_auto, uint64_t* counts, void* stream);
+
+/* Tuning knobs of the counting kernel; zero fields mean "choose". */
+typedef struct wtheta_tune {
+    int32_t threads;           /* threads per block: 128 or 256              */
+    int32_t points_per_thread; /* A points held in registers per thread: 4 or 8 */
+    int32_t hist_mode;         /* 1: private per-thread histograms (no atomics);
+                                  2: per-warp histograms, warp-aggregated atomics */
+    int32_t reserved;
+} wtheta_tune;
+
+/* statistics slots accumulated by wtheta_count_ex (uint64 each) */
+#define WTHETA_STAT_PAIRS 0     /* pairs evaluated, padding included         */
+#define WTHETA_STAT_BINNED 1    /* pairs below the top edge's guard band      */
+#define WTHETA_STAT_RECHECK 2   /* pairs recomputed in FP64                   */
+#define WTHETA_STAT_TILES 3     /* tile pairs processed                       */
+#define WTHETA_NSTATS 4
+
+/*
+ * wtheta_count / wtheta_count_xyz with explicit tuning and statistics.
+ *   coords_are_xyz: 0 = RA/Dec inputs (as wtheta_count), 1 = SoA unit vectors.
+ *   tune: host, may be NULL.
+ *   stats: device, WTHETA_NSTATS uint64, may be NULL; ADDED to (not zeroed).
+ */
+int wtheta_count_ex(const double* coords_a, int64_t n_a, const double* coords_b,
+                    int64_t n_b, int32_t coords_are_xyz, const double* bin_edges_deg,
+                    int32_t n_bins, int32_t is_auto, uint64_t* counts,
+                    const wtheta_tune* tune, uint64_t* stats, void* stream);
+
+/*
+ * RA/Dec (device, interleaved FP64 degrees) -> FP64 unit vectors (device,
+ * SoA 3n doubles): x = cos(dec) cos(ra), y = cos(dec) sin(ra), z = sin(dec).
+ * The conversion every wtheta_count call makes; exposed for testing.
+ */
+int wtheta_radec_to_xyz(const double* ra_dec, int64_t n, double* xyz, void* stream);
+
+/*
+ * Synchronises stream, then reads and clears the calling device's sticky
+ * error word into *code (0 = no problem; else WTHETA_DERR_* bits).
+ */
+int wtheta_get_error(void* stream, uint32_t* code);
+
+/*
+ * Instrumentation (the paper has no counterpart): number of CUDA kernels this
+ * library has launched in the process so far, all devices and streams.
+ */
+uint64_t wtheta_kernel_launches(void);
+
+/*
+ * Landy-Szalay estimator, Eq. 2, w = (DD - 2 DR + RR) / RR, evaluated on
+ * counts normalised by their pair totals (Sec. 2): dd = DD_k / (n_d(n_d-1)/2),
+ * dr = DR_k / (n_d n_r), rr = RR_k / (n_r(n_r-1)/2), then
+ * w_k = ((dd - 2 dr) + rr) / rr in FP64, for k = 1..K.
+ *   DD, DR, RR: host, K+2 slots each (as produced by wtheta_count).
+ *   w: host, K doubles.  Bins with RR_k = 0 give NaN.
+ * Requires n_d >= 2, n_r >= 2.
+ */
+int wtheta_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_t n_d,
+              int64_t n_r, int32_t n_bins, double* w);
+
+/*
+ * Cross-correlation form of the same estimator between catalogues 1 and 2
+ * with their randoms: w = (d1d2 - d1r2 - r1d2 + r1r2) / r1r2, each count
+ * normalised by the product of its catalogue sizes, evaluated in that order.
+ * Host arrays of K+2 slots; w: host, K doubles.
+ */
+int wtheta_ls_cross(const uint64_t* D1D2, const uint64_t* D1R2, const uint64_t* R1D2,
+                    const uint64_t* R1R2, int64_t n_d1, int64_t n_d2, int64_t n_r1,
+                    int64_t n_r2, int32_t n_bins, double* w);
+
+/*
+ * Whole w(theta) from host catalogues: copies data and randoms to the device
+ * on stream, counts DD, DR, RR, copies the counts back and applies
+ * wtheta_ls.  Synchronises stream before returning.
+ *   data, rand: host, interleaved FP64 degrees.
+ *   counts_out: host, 3 (K+2) uint64 (DD, DR, RR), may be NULL.
+ *   w_out: host, K doubles, may be NULL.
+ */
+int wtheta_correlate(const double* data, int64_t n_d, const double* rand, int64_t n_r,
+                     const double* bin_edges_deg, int32_t n_bins, uint64_t* counts_out,
+                     double* w_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WTHETA_H */

@@ -1,0 +1,245 @@
+"""Thin Python binding of libwtheta (include/wtheta.h), same names as the C ABI.
+
+Argument marshalling only: device arrays are torch CUDA tensors (their
+pointers are passed), host arrays are numpy arrays, streams are
+``torch.cuda.Stream`` objects, raw ``cudaStream_t`` integers, or ``None`` for
+torch's current stream.  Every computation happens in libwtheta's CUDA
+kernels; if the library is missing this module raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libwtheta.so")
+HEADER = os.path.join(os.path.dirname(_PKG), "include", "wtheta.h")
+
+WTHETA_OK = 0
+STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUDGET",
+          -6: "EDEVICE"}
+BINS_LINEAR, BINS_LN, BINS_LOG10 = 0, 1, 2
+DERR_NONFINITE, DERR_DEC_RANGE, DERR_NOT_UNIT = 1, 2, 4
+STAT_PAIRS, STAT_BINNED, STAT_RECHECK, STAT_TILES, NSTATS = 0, 1, 2, 3, 4
+
+_lock = threading.Lock()
+_lib = None
+
+
+class WthetaError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__("%s failed: %s (%d)" % (where, STATUS.get(status, "?"), status))
+
+
+class wtheta_tune(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
+                ("hist_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def declared_functions() -> list:
+    """Names of the functions include/wtheta.h declares."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wtheta_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    "libwtheta.so is not built (%s); run python -m paper_1208_3658_gb300.build"
+                    % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+            i64, i32, u32p = ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)
+            u64p = ctypes.POINTER(ctypes.c_uint64)
+            L.wtheta_strerror.restype = ctypes.c_char_p
+            L.wtheta_strerror.argtypes = [ctypes.c_int]
+            L.wtheta_edges.argtypes = [ctypes.c_double, ctypes.c_double, i32, i32, dp]
+            L.wtheta_chord2_edges.argtypes = [dp, i32, dp]
+            L.wtheta_guard_band.argtypes = [dp, i32, u32p, u32p, dp]
+            L.wtheta_count.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
+            L.wtheta_count_xyz.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
+            L.wtheta_count_ex.argtypes = [vp, i64, vp, i64, i32, dp, i32, i32, vp,
+                                          ctypes.POINTER(wtheta_tune), vp, vp]
+            L.wtheta_radec_to_xyz.argtypes = [vp, i64, vp, vp]
+            L.wtheta_get_error.argtypes = [vp, u32p]
+            L.wtheta_ls.argtypes = [u64p, u64p, u64p, i64, i64, i32, dp]
+            L.wtheta_ls_cross.argtypes = [u64p, u64p, u64p, u64p, i64, i64, i64, i64, i32, dp]
+            L.wtheta_correlate.argtypes = [dp, i64, dp, i64, dp, i32, u64p, dp, vp]
+            L.wtheta_kernel_launches.argtypes = []
+            L.wtheta_kernel_launches.restype = ctypes.c_uint64
+            _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+def _check(rc: int, where: str):
+    if rc != WTHETA_OK:
+        raise WthetaError(rc, where)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dev_ptr(t, dtype_size=8, name="array"):
+    """Device pointer of a contiguous CUDA tensor (or None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if t.element_size() != dtype_size:
+        raise ValueError("%s must have %d-byte elements" % (name, dtype_size))
+    return t.data_ptr()
+
+
+def _host_f64(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _host_u64(a):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+def _n_points(t, per_point):
+    if t is None:
+        return 0
+    return t.numel() // per_point
+
+
+# ---------------------------------------------------------------------------
+# entry points
+# ---------------------------------------------------------------------------
+def wtheta_strerror(status: int) -> str:
+    return lib().wtheta_strerror(status).decode()
+
+
+def wtheta_edges(lo_deg: float, hi_deg: float, n_bins: int, mode: int = BINS_LN) -> np.ndarray:
+    e = np.empty(n_bins + 1, np.float64)
+    _check(lib().wtheta_edges(lo_deg, hi_deg, n_bins, mode, _host_f64(e)[1]), "wtheta_edges")
+    return e
+
+
+def wtheta_chord2_edges(edges_deg) -> np.ndarray:
+    e, ep = _host_f64(edges_deg)
+    c = np.empty_like(e)
+    _check(lib().wtheta_chord2_edges(ep, len(e) - 1, _host_f64(c)[1]), "wtheta_chord2_edges")
+    return c
+
+
+def wtheta_guard_band(edges_deg):
+    e, ep = _host_f64(edges_deg)
+    lo = np.empty(len(e), np.uint32)
+    hi = np.empty(len(e), np.uint32)
+    g = np.empty(len(e), np.float64)
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    _check(lib().wtheta_guard_band(ep, len(e) - 1, lo.ctypes.data_as(u32p),
+                                   hi.ctypes.data_as(u32p), _host_f64(g)[1]),
+           "wtheta_guard_band")
+    return lo, hi, g
+
+
+def wtheta_count(ra_dec_a, ra_dec_b, edges_deg, is_auto: bool, counts, stream=None,
+                 n_a: int | None = None, n_b: int | None = None):
+    """ra_dec_*: CUDA float64 tensors [ra0, dec0, ...] (ra_dec_b None for auto);
+    counts: CUDA 8-byte tensor of K+2 slots, overwritten."""
+    e, ep = _host_f64(edges_deg)
+    na = _n_points(ra_dec_a, 2) if n_a is None else n_a
+    nb = (na if is_auto else _n_points(ra_dec_b, 2)) if n_b is None else n_b
+    _check(lib().wtheta_count(_dev_ptr(ra_dec_a), na, _dev_ptr(ra_dec_b), nb, ep, len(e) - 1,
+                              1 if is_auto else 0, _dev_ptr(counts), _stream(stream)),
+           "wtheta_count")
+
+
+def wtheta_count_xyz(xyz_a, xyz_b, edges_deg, is_auto: bool, counts, stream=None,
+                     n_a: int | None = None, n_b: int | None = None):
+    """xyz_*: CUDA float64 tensors, SoA (3, n) contiguous."""
+    e, ep = _host_f64(edges_deg)
+    na = _n_points(xyz_a, 3) if n_a is None else n_a
+    nb = (na if is_auto else _n_points(xyz_b, 3)) if n_b is None else n_b
+    _check(lib().wtheta_count_xyz(_dev_ptr(xyz_a), na, _dev_ptr(xyz_b), nb, ep, len(e) - 1,
+                                  1 if is_auto else 0, _dev_ptr(counts), _stream(stream)),
+           "wtheta_count_xyz")
+
+
+def wtheta_count_ex(coords_a, coords_b, coords_are_xyz: bool, edges_deg, is_auto: bool, counts,
+                    tune: dict | None = None, stats=None, stream=None):
+    e, ep = _host_f64(edges_deg)
+    per = 3 if coords_are_xyz else 2
+    na = _n_points(coords_a, per)
+    nb = na if is_auto else _n_points(coords_b, per)
+    t = None
+    if tune:
+        t = wtheta_tune(int(tune.get("threads", 0)), int(tune.get("points_per_thread", 0)),
+                        int(tune.get("hist_mode", 0)), 0)
+    _check(lib().wtheta_count_ex(_dev_ptr(coords_a), na, _dev_ptr(coords_b), nb,
+                                 1 if coords_are_xyz else 0, ep, len(e) - 1, 1 if is_auto else 0,
+                                 _dev_ptr(counts), ctypes.byref(t) if t is not None else None,
+                                 _dev_ptr(stats), _stream(stream)), "wtheta_count_ex")
+
+
+def wtheta_radec_to_xyz(ra_dec, xyz, stream=None):
+    n = _n_points(ra_dec, 2)
+    _check(lib().wtheta_radec_to_xyz(_dev_ptr(ra_dec), n, _dev_ptr(xyz), _stream(stream)),
+           "wtheta_radec_to_xyz")
+
+
+def wtheta_kernel_launches() -> int:
+    return int(lib().wtheta_kernel_launches())
+
+
+def wtheta_get_error(stream=None) -> int:
+    code = ctypes.c_uint32(0)
+    _check(lib().wtheta_get_error(_stream(stream), ctypes.byref(code)), "wtheta_get_error")
+    return int(code.value)
+
+
+def wtheta_ls(DD, DR, RR, n_d: int, n_r: int) -> np.ndarray:
+    (DD, p1), (DR, p2), (RR, p3) = _host_u64(DD), _host_u64(DR), _host_u64(RR)
+    K = len(DD) - 2
+    w = np.empty(K, np.float64)
+    _check(lib().wtheta_ls(p1, p2, p3, n_d, n_r, K, _host_f64(w)[1]), "wtheta_ls")
+    return w
+
+
+def wtheta_ls_cross(D1D2, D1R2, R1D2, R1R2, n_d1, n_d2, n_r1, n_r2) -> np.ndarray:
+    arrs = [_host_u64(x) for x in (D1D2, D1R2, R1D2, R1R2)]
+    K = len(arrs[0][0]) - 2
+    w = np.empty(K, np.float64)
+    _check(lib().wtheta_ls_cross(*[p for _, p in arrs], n_d1, n_d2, n_r1, n_r2, K,
+                                 _host_f64(w)[1]), "wtheta_ls_cross")
+    return w
+
+
+def wtheta_correlate(data, rand, edges_deg, stream=None):
+    """Host catalogues in, (counts (3, K+2) uint64, w (K,)) out, one call."""
+    d, dp = _host_f64(data)
+    r, rp = _host_f64(rand)
+    e, ep = _host_f64(edges_deg)
+    K = len(e) - 1
+    counts = np.zeros(3 * (K + 2), np.uint64)
+    w = np.empty(K, np.float64)
+    _check(lib().wtheta_correlate(dp, len(d) // 2, rp, len(r) // 2, ep, K, _host_u64(counts)[1],
+                                  _host_f64(w)[1], _stream(stream)), "wtheta_correlate")
+    return counts.reshape(3, K + 2), w

@@ -1,0 +1,184 @@
+"""The C-ABI library on the CPU: it loads, exports every declared symbol, and
+its host-side arithmetic (edges, squared-chord edges, estimators, argument
+validation, guard band) agrees with the oracle and with the FP32 error bound.
+No kernel is launched here."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1208_3658_gb300 import synth
+from paper_1208_3658_gb300 import wtheta as W
+
+ARCMIN = 1.0 / 60.0
+EDGE_SETS = [
+    (1.0 * ARCMIN, 5.0, 16, W.BINS_LN),
+    (0.5 * ARCMIN, 20.0, 32, W.BINS_LN),
+    (1.0 * ARCMIN, 10.0, 24, W.BINS_LOG10),
+    (0.2 * ARCMIN, 30.0, 64, W.BINS_LN),
+    (0.0, 180.0, 12, W.BINS_LINEAR),
+    (0.0, 180.0, 256, W.BINS_LINEAR),
+    (1e-4, 179.0, 200, W.BINS_LN),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_1208_3658_gb300 import build
+    build.build()
+
+
+def test_exports_every_declared_symbol():
+    L = W.lib()
+    names = W.declared_functions()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("lo,hi,K,mode", EDGE_SETS)
+def test_edges_and_chords_bit_equal_to_oracle(lo, hi, K, mode):
+    e = W.wtheta_edges(lo, hi, K, mode)
+    assert np.array_equal(e, O.edges(lo, hi, K, mode))
+    assert np.array_equal(W.wtheta_chord2_edges(e), O.chord2(e))
+
+
+def test_ls_matches_oracle():
+    wl = synth.small(n=1500)
+    e = O.edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    DD, DR, RR, w_o = O.wtheta(wl.data, wl.rand, e)
+    w = W.wtheta_ls(DD, DR, RR, wl.n_d, wl.n_r)
+    scale = np.maximum(np.abs(w_o), DD[1:-1] / RR[1:-1] + 2 * DR[1:-1] / RR[1:-1] + 1)
+    ok = RR[1:-1] > 0
+    assert np.all(np.abs(w - w_o)[ok] <= 1e-12 * scale[ok])
+    wc = W.wtheta_ls_cross(DD, DR, DR, RR, 10, 20, 30, 40)
+    wco = O.ls_cross(DD, DR, DR, RR, 10, 20, 30, 40)
+    assert np.allclose(wc[ok], wco[ok], rtol=1e-12, atol=0)
+
+
+def test_ls_closed_form_d_equals_r():
+    """Counts with R = D give w = 2/n (derivation in oracle_pins)."""
+    n = 500
+    D = synth.clustered(synth.Patch(0, 5, 0, 5), n, 10, 3.0, 2, "test", "data")
+    e = O.edges(1.0 * ARCMIN, 5.0, 16)
+    DD = O.count(D, None, e, True)
+    DR = O.count(D, D, e, False)
+    w = W.wtheta_ls(DD, DR, DD, n, n)
+    nz = DD[1:-1] > 0
+    assert np.all(np.abs(w[nz] - 2.0 / n) <= 3e-12)
+
+
+def test_argument_validation_needs_no_gpu():
+    L = W.lib()
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    dp = ctypes.POINTER(ctypes.c_double)
+    ep = e.ctypes.data_as(dp)
+    EINVAL = -1
+    # bad edge arrays
+    for bad in ([1.0, 1.0], [2.0, 1.0], [-1.0, 1.0], [1.0, 181.0], [0.0, np.nan]):
+        b = np.array(bad, np.float64)
+        assert L.wtheta_chord2_edges(b.ctypes.data_as(dp), 1, b.ctypes.data_as(dp)) == EINVAL
+    assert L.wtheta_edges(1.0, 0.5, 4, 1, ep) == EINVAL
+    assert L.wtheta_edges(0.0, 5.0, 4, 1, ep) == EINVAL       # log bins need lo > 0
+    assert L.wtheta_edges(1.0, 5.0, 0, 1, ep) == EINVAL
+    assert L.wtheta_edges(1.0, 5.0, 257, 0, np.empty(258).ctypes.data_as(dp)) == EINVAL
+    # counting: bad sizes and pointers are rejected before any device work
+    c = ctypes.c_void_p(16)
+    assert L.wtheta_count(None, 5, None, 0, ep, 16, 1, c, None) == EINVAL       # null a, n > 0
+    assert L.wtheta_count(c, 5, None, 0, ep, 16, 1, None, None) == EINVAL       # null counts
+    assert L.wtheta_count(c, -1, None, 0, ep, 16, 1, c, None) == EINVAL
+    assert L.wtheta_count(c, 5, c, 4, ep, 16, 1, c, None) == EINVAL             # auto, n_b != n_a
+    assert L.wtheta_count(c, 5, None, 3, ep, 16, 0, c, None) == EINVAL          # cross, null b
+    assert L.wtheta_count(c, 5, c, 5, ep, 16, 2, c, None) == EINVAL             # is_auto not 0/1
+    assert L.wtheta_count(c, 5, c, 5, ep, 0, 0, c, None) == EINVAL              # K = 0
+    u = np.zeros(18, np.uint64).ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    w = np.zeros(16).ctypes.data_as(dp)
+    assert L.wtheta_ls(u, u, u, 1, 5, 16, w) == EINVAL                          # n_d < 2
+    assert W.wtheta_strerror(EINVAL) == "invalid argument"
+
+
+def _emulate_s32(A, B):
+    """The kernel's FP32 squared chord: d = fl32(a) - fl32(b) in FP32,
+    s = fma(dz, dz, fma(dy, dy, dx*dx)).  Each fma is emulated as an exact FP64
+    sum (d^2 is exact in FP64) rounded to FP32; where that FP64 sum itself
+    rounds, the emulation can differ from a true fma by one FP32 ulp, which the
+    bound's factor-2 margin covers."""
+    a = A.astype(np.float32)
+    b = B.astype(np.float32)
+    d = a - b
+    p = d[0] * d[0]
+    q = (d[1].astype(np.float64) ** 2 + p.astype(np.float64)).astype(np.float32)
+    return (d[2].astype(np.float64) ** 2 + q.astype(np.float64)).astype(np.float32)
+
+
+def _s64(A, B):
+    d = A - B
+    return ((d[0] * d[0]) + (d[1] * d[1])) + (d[2] * d[2])
+
+
+def _pairs_at(theta_deg, rng):
+    """Unit-vector pairs (FP64) at angular separation theta (radians from deg)."""
+    n = len(theta_deg)
+    a = rng.normal(size=(3, n))
+    a /= np.linalg.norm(a, axis=0)
+    t = rng.normal(size=(3, n))
+    t -= a * np.sum(a * t, axis=0)
+    t /= np.linalg.norm(t, axis=0)
+    th = np.radians(theta_deg)
+    b = a * np.cos(th) + t * np.sin(th)
+    return a, b
+
+
+@pytest.mark.parametrize("lo,hi,K,mode", EDGE_SETS)
+def test_guard_band_classification_is_sound(lo, hi, K, mode):
+    """For pairs near every edge (relative offsets 1e-12..1e-2 either side) and
+    at random separations: an FP32 value below the band is below the FP64 edge,
+    one above the band at or above it.  No pair is misclassified."""
+    rng = np.random.default_rng(12345 + K)
+    e = W.wtheta_edges(lo, hi, K, mode)
+    c = W.wtheta_chord2_edges(e)
+    lo_b, hi_b, g = W.wtheta_guard_band(e)
+    assert np.all(g > 0) and np.all(lo_b <= hi_b)
+    n_in_band = 0
+    total = 0
+    for k in range(K + 1):
+        if e[k] == 0.0:
+            continue
+        rel = np.concatenate([-np.logspace(-12, -2, 600), np.logspace(-12, -2, 600)])
+        theta = np.clip(e[k] * (1 + rel), 1e-9, 180.0)
+        A, B = _pairs_at(theta, rng)
+        s32 = _emulate_s32(A, B)
+        s64 = _s64(A, B)
+        bits = s32.view(np.uint32)
+        below = bits < lo_b[k]
+        above = bits > hi_b[k]
+        assert np.all(s64[below] < c[k]), (k, np.nonzero(s64[below] >= c[k]))
+        assert np.all(s64[above] >= c[k]), (k, np.nonzero(s64[above] < c[k]))
+        n_in_band += int(np.sum(~below & ~above))
+        total += len(theta)
+    assert n_in_band < total  # the band is narrow: most offsets >= 1e-5 resolve in FP32
+
+
+def test_fp32_error_bound_random_pairs():
+    """|s32 - s64| <= g(c)/2 whenever c <= s64 <= 2c, over pairs at all
+    scales (the half-width doubles the bound E(s), evaluated at 2c)."""
+    rng = np.random.default_rng(7)
+    theta = 10 ** rng.uniform(-5, np.log10(180.0), 400_000)
+    A, B = _pairs_at(theta, rng)
+    s32 = _emulate_s32(A, B).astype(np.float64)
+    s64 = _s64(A, B)
+    # edges at each pair's own separation scale, c = s64 / 1.5 (so c <= s <= 2c)
+    e = np.sort(np.degrees(2 * np.arcsin(np.sqrt(s64 / 1.5) / 2)))
+    e = np.unique(e[(e > 0) & (e < 180)])
+    idx = np.linspace(0, len(e) - 1, 200).astype(int)
+    sub = np.unique(e[idx])
+    _, _, g = W.wtheta_guard_band(sub)
+    cs = W.wtheta_chord2_edges(sub)
+    # each pair: use the edge just below s64/1.5 ... 2c range
+    j = np.searchsorted(cs, s64 / 2, side="left")
+    ok = (j < len(cs)) & (cs[np.minimum(j, len(cs) - 1)] <= s64)
+    jj = np.minimum(j, len(cs) - 1)[ok]
+    err = np.abs(s32 - s64)[ok]
+    assert ok.sum() > 100_000
+    assert np.all(err <= g[jj] / 2), np.max(err / (g[jj] / 2))

@@ -1,0 +1,272 @@
+"""GPU counts against the CPU oracle, through the C ABI.
+
+P1 (zero tolerance): wtheta_count_xyz is fed the oracle's own FP64 unit
+vectors; counts must be bit-identical.
+P2: wtheta_count converts RA/Dec on the device (CUDA sin/cos may differ from
+the host's in the last place); counts must be bit-identical when the oracle
+finds no pair within a few ulps of an edge, otherwise differ by at most that
+many pairs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1208_3658_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ARCMIN = 1.0 / 60.0
+VARIANTS = [dict(threads=t, points_per_thread=r, hist_mode=h)
+            for t in (128, 256) for r in (4, 8) for h in (1, 2)]
+
+
+@pytest.fixture(scope="module")
+def W():
+    from paper_1208_3658_gb300 import build
+    build.build()
+    from paper_1208_3658_gb300 import wtheta
+    assert torch.cuda.is_available()
+    return wtheta
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def gpu_count_xyz(W, A, B, e, is_auto, tune=None, stats=None):
+    c = torch.zeros(len(e) + 1, dtype=torch.int64, device="cuda")
+    a = dev(A)
+    b = None if is_auto else dev(B)
+    if tune is None and stats is None:
+        W.wtheta_count_xyz(a, b, e, is_auto, c)
+    else:
+        W.wtheta_count_ex(a, b, True, e, is_auto, c, tune=tune, stats=stats)
+    torch.cuda.synchronize()
+    return c.cpu().numpy().astype(np.uint64)
+
+
+def gpu_count(W, rd_a, rd_b, e, is_auto, tune=None, stats=None):
+    c = torch.zeros(len(e) + 1, dtype=torch.int64, device="cuda")
+    a = dev(rd_a)
+    b = None if is_auto else dev(rd_b)
+    if tune is None and stats is None:
+        W.wtheta_count(a, b, e, is_auto, c)
+    else:
+        W.wtheta_count_ex(a, b, False, e, is_auto, c, tune=tune, stats=stats)
+    torch.cuda.synchronize()
+    return c.cpu().numpy().astype(np.uint64)
+
+
+def test_radec_conversion_within_ulps(W):
+    rng = np.random.default_rng(3)
+    n = 200_000
+    ra = np.concatenate([rng.uniform(-720, 720, n - 8), [0, 90, 180, 270, 359.999999, 360, -0.0, 1e-9]])
+    dec = np.concatenate([rng.uniform(-90, 90, n - 8), [90, -90, 0, 45, -45, 89.9999999, -89.9999, 0]])
+    rd = synth.interleave(ra, dec)
+    want = O.radec_to_xyz(rd)
+    x = torch.empty(3 * n, dtype=torch.float64, device="cuda")
+    W.wtheta_radec_to_xyz(dev(rd), x)
+    torch.cuda.synchronize()
+    got = x.cpu().numpy().reshape(3, n)
+    ulp = np.spacing(np.maximum(np.abs(want), 2.0 ** -60))
+    assert np.max(np.abs(got - want) / ulp) <= 4.0
+
+
+@pytest.mark.parametrize("tune", VARIANTS, ids=lambda t: "nt%d_r%d_h%d" % (
+    t["threads"], t["points_per_thread"], t["hist_mode"]))
+def test_small_workload_bit_exact_p1(W, tune):
+    """10k clustered + 10k random in a 10 deg patch, 16 log bins 1'-5 deg."""
+    wl = synth.small()
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    D, R = O.radec_to_xyz(wl.data), O.radec_to_xyz(wl.rand)
+    for A, B, auto in [(D, None, True), (D, R, False), (R, None, True)]:
+        want = O.count_xyz(A, B, e, auto)
+        got = gpu_count_xyz(W, A, B, e, auto, tune=tune)
+        assert np.array_equal(got, want), (auto, got, want)
+
+
+def test_small_workload_radec_p2_and_w(W):
+    wl = synth.small()
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    D, R = O.radec_to_xyz(wl.data), O.radec_to_xyz(wl.rand)
+    got = []
+    for a, b, A, B, auto in [(wl.data, None, D, None, True), (wl.data, wl.rand, D, R, False),
+                             (wl.rand, None, R, None, True)]:
+        want = O.count_xyz(A, B, e, auto)
+        amb = O.count_ambiguous_xyz(A, B, e, auto)
+        g = gpu_count(W, a, b, e, auto)
+        if amb == 0:
+            assert np.array_equal(g, want)
+        else:
+            assert np.sum(np.abs(g.astype(np.int64) - want.astype(np.int64))) <= 2 * amb
+        assert int(g.sum()) == int(want.sum())
+        got.append(g)
+    w = W.wtheta_ls(*got, wl.n_d, wl.n_r)
+    DD, DR, RR, w_o = O.wtheta(wl.data, wl.rand, e)
+    scale = np.maximum(np.abs(w_o), DD[1:-1] / RR[1:-1] + 2 * DR[1:-1] / RR[1:-1] + 1)
+    assert np.all(np.abs(w - w_o) <= 1e-12 * scale)
+
+
+SIZES = [0, 1, 2, 31, 33, 511, 512, 513, 1023, 1024, 1025, 2047, 2049, 4097]
+
+
+@pytest.mark.parametrize("n", SIZES)
+def test_ragged_sizes_bit_exact(W, n):
+    fp = synth.Patch(10.0, 3.0, -5.0, -2.0)
+    a = synth.clustered(fp, n, max(1, n // 40), 2.0, 5, "test", "data", n) if n else np.zeros(0)
+    b = synth.uniform(fp, n + 7, 6, "test", "random", n)
+    e = W.wtheta_edges(0.5 * ARCMIN, 2.0, 20)
+    A = O.radec_to_xyz(a) if n else np.zeros((3, 0))
+    B = O.radec_to_xyz(b)
+    for tune in (VARIANTS[0], VARIANTS[3], VARIANTS[6]):
+        got = gpu_count_xyz(W, A, None, e, True, tune=tune)
+        want = O.count_xyz(A, None, e, True)
+        assert np.array_equal(got, want), ("auto", n, got, want)
+        assert int(got.sum()) == n * (n - 1) // 2
+        got = gpu_count_xyz(W, A, B, e, False, tune=tune)
+        want = O.count_xyz(A, B, e, False)
+        assert np.array_equal(got, want), ("cross", n, got, want)
+
+
+def test_hand_placed_points(W):
+    import oracle_pins
+    rows = [l.split() for l in open(oracle_pins.GOLDEN + "/hand_placed.txt")
+            if l.strip() and not l.startswith("#")]
+    for name, (lo, hi, K, mode) in oracle_pins.GOLDEN_EDGES.items():
+        e = W.wtheta_edges(lo, hi, K, mode)
+        sel = [r for r in rows if r[0] == name]
+        for r in sel:
+            a = np.array([float(r[1]), float(r[2])])
+            b = np.array([float(r[3]), float(r[4])])
+            got = gpu_count(W, a, b, e, False)
+            want = np.zeros(K + 2, np.uint64)
+            want[oracle_pins._slot_by_angle(e, float(r[5]))] = 1
+            assert np.array_equal(got, want), (name, r, got)
+
+
+def test_coincident_points_and_linear_bins_from_zero(W):
+    rng = np.random.default_rng(11)
+    base = synth.uniform(synth.Patch(0, 20, 0, 20), 700, 9, "test", "random")
+    dup = np.concatenate([base, base[: 2 * 300]])  # 300 exact duplicates
+    e = W.wtheta_edges(0.0, 180.0, 12, W.BINS_LINEAR)
+    A = O.radec_to_xyz(dup)
+    got = gpu_count_xyz(W, A, None, e, True)
+    want = O.count_xyz(A, None, e, True)
+    assert np.array_equal(got, want)
+    assert got[0] == 0  # e_0 = 0: nothing below the first edge
+    del rng
+
+
+def test_pathological_edges_take_recheck_path(W):
+    """256 linear bins to 180 deg: squared-chord edges crowd together near 4,
+    the screening table marks those buckets for FP64 recheck; still exact."""
+    e = W.wtheta_edges(0.0, 180.0, 256, W.BINS_LINEAR)
+    R = O.radec_to_xyz(synth.uniform(synth.FullSky(), 3000, 10, "test", "random"))
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    got = gpu_count_xyz(W, R, None, e, True, tune=dict(hist_mode=2), stats=stats)
+    want = O.count_xyz(R, None, e, True)
+    assert np.array_equal(got, want)
+    assert int(stats[W.STAT_RECHECK]) > 0
+
+
+def test_pairs_straddling_every_edge(W):
+    """Pairs placed at e_k (1 +- delta), delta down to 1e-12: the FP32 value
+    is ambiguous and the FP64 recheck must reproduce the oracle exactly."""
+    rng = np.random.default_rng(21)
+    e = W.wtheta_edges(0.5 * ARCMIN, 20.0, 32)
+    A_list, B_list = [], []
+    for k in range(len(e)):
+        for d in np.concatenate([-np.logspace(-12, -3, 40), np.logspace(-12, -3, 40), [0.0]]):
+            th = math.radians(e[k] * (1 + d))
+            a = rng.normal(size=3)
+            a /= np.linalg.norm(a)
+            t = rng.normal(size=3)
+            t -= a * (a @ t)
+            t /= np.linalg.norm(t)
+            A_list.append(a)
+            B_list.append(a * math.cos(th) + t * math.sin(th))
+    A = np.ascontiguousarray(np.array(A_list).T)
+    B = np.ascontiguousarray(np.array(B_list).T)
+    # one pair per column: compare pair-by-pair through the cross count of
+    # single points, batched as a diagonal: count all pairs, then the
+    # aligned subset via separate calls would be slow; instead check the full
+    # cross count (contains all aligned pairs) and the aligned pairs alone
+    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    got = gpu_count_xyz(W, A, B, e, False, stats=stats)
+    want = O.count_xyz(A, B, e, False)
+    assert np.array_equal(got, want)
+    assert int(stats[W.STAT_RECHECK]) > 0
+    for i in range(0, A.shape[1], 97):
+        g = gpu_count_xyz(W, A[:, i:i + 1], B[:, i:i + 1], e, False)
+        w = O.count_xyz(A[:, i:i + 1], B[:, i:i + 1], e, False)
+        assert np.array_equal(g, w), i
+
+
+def test_cross_is_symmetric(W):
+    wl = synth.small(n=5000)
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    ab = gpu_count(W, wl.data, wl.rand, e, False)
+    ba = gpu_count(W, wl.rand, wl.data, e, False)
+    assert np.array_equal(ab, ba)
+
+
+def test_device_error_word(W):
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    W.wtheta_get_error()  # clear
+    bad = np.array([10.0, 20.0, np.nan, 5.0, 30.0, 40.0])
+    gpu_count(W, bad, None, e, True)
+    assert W.wtheta_get_error() & W.DERR_NONFINITE
+    assert W.wtheta_get_error() == 0  # read clears
+    bad = np.array([10.0, 95.0, 11.0, 20.0])
+    gpu_count(W, bad, None, e, True)
+    assert W.wtheta_get_error() & W.DERR_DEC_RANGE
+
+
+def test_correlate_host_api(W):
+    wl = synth.small(n=4000)
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    counts, w = W.wtheta_correlate(wl.data, wl.rand, e)
+    DD, DR, RR, w_o = O.wtheta(wl.data, wl.rand, e)
+    D, R = O.radec_to_xyz(wl.data), O.radec_to_xyz(wl.rand)
+    amb = (O.count_ambiguous_xyz(D, None, e, True) + O.count_ambiguous_xyz(D, R, e, False)
+           + O.count_ambiguous_xyz(R, None, e, True))
+    if amb == 0:
+        assert np.array_equal(counts, np.stack([DD, DR, RR]))
+        assert np.all(np.abs(w - w_o) <= 1e-12 * np.maximum(np.abs(w_o), 4.0))
+
+
+def test_survey_workload_full_size(W):
+    """1M clustered + 1M random in a 60 deg cap, 32 log bins 0.5'-20 deg, in
+    the benchmark's launch configuration: exact totals, DR = RD, additivity
+    DD(A) = DD(A1) + DD(A2) + DR(A1, A2), and a sampled block of rows against
+    the oracle."""
+    wl = synth.survey()
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    nd, nr = wl.n_d, wl.n_r
+    DD = gpu_count(W, wl.data, None, e, True)
+    DR = gpu_count(W, wl.data, wl.rand, e, False)
+    RR = gpu_count(W, wl.rand, None, e, True)
+    assert int(DD.sum()) == nd * (nd - 1) // 2
+    assert int(RR.sum()) == nr * (nr - 1) // 2
+    assert int(DR.sum()) == nd * nr
+    RD = gpu_count(W, wl.rand, wl.data, e, False)
+    assert np.array_equal(DR, RD)
+    h = 2 * 400_003
+    a1, a2 = wl.data[:h], wl.data[h:]
+    parts = (gpu_count(W, a1, None, e, True).astype(np.int64)
+             + gpu_count(W, a2, None, e, True).astype(np.int64)
+             + gpu_count(W, a1, a2, e, False).astype(np.int64))
+    assert np.array_equal(parts.astype(np.uint64), DD)
+    # sampled rows against the oracle (P1: the oracle's own unit vectors)
+    D = O.radec_to_xyz(wl.data)
+    R = O.radec_to_xyz(wl.rand)
+    rows = np.sort(np.random.default_rng(5).choice(nd, 1500, replace=False))
+    As = np.ascontiguousarray(D[:, rows])
+    got = gpu_count_xyz(W, As, R, e, False)
+    want = O.count_xyz(As, R, e, False)
+    assert np.array_equal(got, want)
+    w = W.wtheta_ls(DD, DR, RR, nd, nr)
+    assert np.all(np.isfinite(w))
