@@ -46,11 +46,18 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["survey", "small", "largest"], default="survey")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n", type=int, default=0,
+                    help="points per catalogue (same shape, smaller: profiling cases)")
     return ap.parse_args()
 
 
-def make_workload(name, seed):
+def make_workload(name, seed, n=0):
     from paper_1208_3658_gb300 import synth
+    if n:
+        wl = {"small": synth.small, "survey": synth.survey, "largest": synth.largest}[name](
+            seed=seed, n=n)
+        return wl, "%s-shaped, %d + %d points" % (name, wl.n_d, wl.n_r)
     if name == "small":
         wl = synth.small(seed=seed)
         desc = ("small: 10k clustered (200 centres, sigma 3') + 10k uniform, 10x10 deg patch, "
@@ -185,7 +192,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
-    wl, desc = make_workload(args.workload, seed=1 + rank)
+    wl, desc = make_workload(args.workload, seed=1 + rank, n=args.n)
     e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
     K = wl.n_bins
     d_data = torch.from_numpy(wl.data).to(dev)
@@ -301,6 +308,8 @@ def run_ours(args, rank, world, dist):
     }
 
     # end to end through the host-buffer C-ABI call (H2D + count + D2H + LS)
+    if args.no_e2e:
+        return out
     h_data = torch.from_numpy(wl.data).pin_memory()
     h_rand = torch.from_numpy(wl.rand).pin_memory()
     W.wtheta_correlate(h_data.numpy(), h_rand.numpy(), e, stream=stream)
@@ -328,7 +337,7 @@ def run_reference(args, rank, world):
     """The CPU oracle on the host cores, each step a bounded sample (data rows
     against all randoms) of the same workload."""
     from oracle import oracle as O
-    wl, desc = make_workload(args.workload, seed=1)
+    wl, desc = make_workload(args.workload, seed=1, n=args.n)
     e = O.edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
     cal = oracle_sample_rate(wl, e, target_s=4.0)
     import numpy as np
