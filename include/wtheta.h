@@ -54,6 +54,7 @@ extern "C" {
 #define WTHETA_ETIMEOUT (-4) /* a bounded device or host wait gave up        */
 #define WTHETA_EBUDGET (-5)  /* a request does not fit the memory budget     */
 #define WTHETA_EDEVICE (-6)  /* the device error word is non-zero            */
+#define WTHETA_ESIZE (-7)    /* input larger than a fixed-capacity entry point takes */
 
 /* bits of the device error word (wtheta_get_error) */
 #define WTHETA_DERR_NONFINITE 1u  /* an input coordinate is NaN or infinite  */
@@ -157,6 +158,40 @@ int wtheta_count_ex(const double* coords_a, int64_t n_a, const double* coords_b,
                     int64_t n_b, int32_t coords_are_xyz, const double* bin_edges_deg,
                     int32_t n_bins, int32_t is_auto, uint64_t* counts,
                     const wtheta_tune* tune, uint64_t* stats, void* stream);
+
+/*
+ * Allocation-free variant of wtheta_count_xyz (the paper has no counterpart).
+ *
+ * Some callers cannot let a library allocate device memory: a process whose
+ * framework already owns the device's memory in its own pool (so a library
+ * cudaMalloc fails or breaks its accounting), a server that reserves a fixed
+ * memory budget up front, or a latency-bound loop that cannot afford an
+ * allocation's implicit synchronisation.  This entry point allocates nothing:
+ * it calls no cudaMalloc, cudaMallocAsync, cudaFree or allocating library
+ * routine.  The caller passes the inputs and the output; the only scratch
+ * (FP32 copies of both catalogues and a work cursor) lives in one fixed
+ * device array inside libwtheta, 256 B + 16 B x WTHETA_NOALLOC_MAX_POINTS
+ * (about 4 MiB), which every device that loads the library holds until the
+ * process exits.
+ *
+ * Arguments, result and exactness are those of wtheta_count_xyz (same
+ * kernels, same counts).  Limit: with n rounded up to a whole tile of
+ * WTHETA_NOALLOC_TILE points, round_up(n_a) + round_up(n_b) (auto: round_up(n_a)
+ * alone) must not exceed WTHETA_NOALLOC_MAX_POINTS; larger inputs return
+ * WTHETA_ESIZE and nothing is launched.
+ *
+ * The first call on a device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call on each device
+ * before any stream capture.  Every call reuses the same array, which keeps
+ * the previous call's contents (each call rewrites what it reads and clears
+ * its cursor): calls whose work can overlap on the GPU, from several streams
+ * or host threads, race on the array and give wrong counts, so serialise them.
+ */
+#define WTHETA_NOALLOC_MAX_POINTS 262144
+#define WTHETA_NOALLOC_TILE 1024
+int wtheta_count_xyz_noalloc(const double* xyz_a, int64_t n_a, const double* xyz_b,
+                             int64_t n_b, const double* bin_edges_deg, int32_t n_bins,
+                             int32_t is_auto, uint64_t* counts, void* stream);
 
 /*
  * RA/Dec (device, interleaved FP64 degrees) -> FP64 unit vectors (device,

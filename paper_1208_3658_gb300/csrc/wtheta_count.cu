@@ -577,6 +577,113 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     return rc;
 }
 
+// ---------------------------------------------------------------------------
+// allocation-free variant of the xyz count
+// ---------------------------------------------------------------------------
+// The fixed scratch of wtheta_count_xyz_noalloc: a 256-byte head holding the
+// work cursor, then FP32 float4 copies of catalogue a and (cross counts)
+// catalogue b, each padded to whole tiles.  It is loaded with the library's
+// module on every device that uses it and lives until the process exits.
+static __device__ __align__(256) unsigned char
+    g_noalloc_scratch[256 + 16 * (size_t)WTHETA_NOALLOC_MAX_POINTS];
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol names a host-side stand-in, not device memory, so the address is
+// looked up once per device (with that device current) and cached.
+static int noalloc_scratch(unsigned char** out) {
+    static std::mutex mu;
+    static void* addr[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return WTHETA_ECUDA;
+    std::lock_guard<std::mutex> g(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return WTHETA_ECUDA;
+        addr[dev] = p;
+    }
+    *out = (unsigned char*)addr[dev];
+    return WTHETA_OK;
+}
+
+static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double* cb,
+                                  long long n_b, const double* edges, int K, int is_auto,
+                                  unsigned long long* counts, cudaStream_t st) {
+    if (!counts || n_a < 0 || n_b < 0 || (is_auto != 0 && is_auto != 1)) return WTHETA_EINVAL;
+    if (n_a > 0 && !ca) return WTHETA_EINVAL;
+    if (is_auto) {
+        if (cb && cb != ca) return WTHETA_EINVAL;
+        if (n_b != n_a && !(cb == nullptr && n_b == 0)) return WTHETA_EINVAL;
+        cb = ca;
+        n_b = n_a;
+    } else if (n_b > 0 && !cb) {
+        return WTHETA_EINVAL;
+    }
+    const long long T = WTHETA_NOALLOC_TILE;
+    const long long pa = round_up(n_a, T), pb = is_auto ? 0 : round_up(n_b, T);
+    if (pa + pb > (long long)WTHETA_NOALLOC_MAX_POINTS) return WTHETA_ESIZE;
+    static thread_local BinTable tab;
+    int rc = build_table(edges, K, &tab);
+    if (rc) return rc;
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    unsigned char* base = nullptr;
+    if ((rc = noalloc_scratch(&base))) return rc;
+
+    if ((rc = check_cuda(cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * (K + 2), st))))
+        return rc;
+    const unsigned long long total =
+        is_auto ? (unsigned long long)n_a * (unsigned long long)(n_a > 0 ? n_a - 1 : 0) / 2ull
+                : (unsigned long long)n_a * (unsigned long long)n_b;
+    const bool empty = is_auto ? n_a < 2 : (n_a == 0 || n_b == 0);
+    if (empty) {
+        k_finalize<<<1, 1, 0, st>>>(counts, K, total);
+        count_launch();
+        return check_cuda(cudaGetLastError());
+    }
+    wtheta_tune fixed = {128, 8, 0, 0};  // the tile of WTHETA_NOALLOC_TILE points
+    const Variant* v = pick_variant(&fixed, K, tab.n_lut, di.max_smem_optin);
+    if (!v || (long long)v->nt * v->r != T) return WTHETA_EINVAL;
+
+    unsigned long long* cursor = (unsigned long long*)base;
+    float4* a32 = (float4*)(base + 256);
+    float4* b32 = is_auto ? a32 : a32 + pa;
+    const int cvt_threads = 256;
+    auto cvt_grid = [&](long long n) {
+        long long g = (n + cvt_threads - 1) / cvt_threads;
+        return (int)std::min<long long>(std::max<long long>(g, 1), (long long)di.sm_count * 16);
+    };
+    // every word the kernels read is rewritten here: both padded copies and the cursor
+    k_xyz_to_f32<<<cvt_grid(pa), cvt_threads, 0, st>>>(ca, n_a, pa, a32, 1.f);
+    count_launch();
+    if (!is_auto) {
+        k_xyz_to_f32<<<cvt_grid(pb), cvt_threads, 0, st>>>(cb, n_b, pb, b32, -1.f);
+        count_launch();
+    }
+    if ((rc = check_cuda(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st)))) return rc;
+    const long long ta = pa / T, tb = is_auto ? ta : pb / T;
+    const long long n_items = is_auto ? ta * (ta + 1) / 2 : ta * tb;
+    const size_t smem = v->smem(K, tab.n_lut);
+    int grid = 0;
+    if ((rc = grid_for(v, smem, n_items, di.sm_count, &grid))) return rc;
+    PairParams prm;
+    std::memset(&prm, 0, sizeof(prm));
+    prm.a32 = a32; prm.b32 = b32; prm.a64 = ca; prm.b64 = cb;
+    prm.a64_stride = n_a; prm.b64_stride = n_b;
+    prm.tiles_a = ta; prm.tiles_b = tb; prm.n_items = n_items;
+    prm.is_auto = is_auto;
+    const unsigned long long per_item = (v->hm == kHistLane ? 1ull : 32ull) * (unsigned long long)T;
+    prm.items_per_flush = (int)std::min<unsigned long long>(0xFFFFFFFFull / per_item, 1ull << 30);
+    prm.cursor = cursor; prm.counts = counts; prm.stats = nullptr;
+    std::memcpy(&prm.tab, &tab, sizeof(tab));
+    v->kernel<<<grid, v->nt, smem, st>>>(prm);
+    count_launch();
+    if ((rc = check_cuda(cudaGetLastError()))) return rc;
+    k_finalize<<<1, 1, 0, st>>>(counts, K, total);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
 }  // namespace wtheta
 
 using namespace wtheta;
@@ -611,6 +718,13 @@ int wtheta_radec_to_xyz(const double* rd, int64_t n, double* xyz, void* stream) 
     k_radec_to_xyz<<<grid, threads, 0, (cudaStream_t)stream>>>(rd, n, n, xyz, n, nullptr, 1.f);
     count_launch();
     return check_cuda(cudaGetLastError());
+}
+
+int wtheta_count_xyz_noalloc(const double* a, int64_t n_a, const double* b, int64_t n_b,
+                             const double* edges, int32_t K, int32_t is_auto, uint64_t* counts,
+                             void* stream) {
+    return count_xyz_noalloc_impl(a, n_a, b, n_b, edges, K, is_auto, (unsigned long long*)counts,
+                                  (cudaStream_t)stream);
 }
 
 uint64_t wtheta_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

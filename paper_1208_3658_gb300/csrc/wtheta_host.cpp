@@ -99,17 +99,18 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
     t->K = K;
     chord2_edges(edges_deg, K, t->c64);
     struct Band { uint32_t lo, hi; int k; };
-    std::vector<Band> bands;
+    Band bands[kMaxBins + 1];
+    size_t n_bands = 0;
     for (int k = 0; k <= K; ++k) {
         if (t->c64[k] == 0.0) continue;
         Band b;
         guard_bounds(t->c64[k], &b.lo, &b.hi, nullptr);
         b.k = k;
-        bands.push_back(b);
+        bands[n_bands++] = b;
     }
     // K >= 1 and the edges increase, so c_K > 0 and there is at least one band.
-    t->h_top = bands.back().hi;
-    const uint32_t lo_first = bands.front().lo;
+    t->h_top = bands[n_bands - 1].hi;
+    const uint32_t lo_first = bands[0].lo;
     int best_shift = -1, best_complex = 1 << 30;
     for (int shift = 30; shift >= 0; --shift) {
         long long n = (long long)(t->h_top >> shift) - (long long)(lo_first >> shift) + 1;
@@ -118,7 +119,8 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
         int complex_buckets = 0;
         long long prev_bucket = -1;
         int prev_count = 0;
-        for (const Band& b : bands) {
+        for (size_t i = 0; i < n_bands; ++i) {
+            const Band& b = bands[i];
             long long b0 = b.lo >> shift, b1 = b.hi >> shift;
             for (long long q = b0; q <= b1; ++q) {
                 if (q == prev_bucket) {
@@ -144,13 +146,13 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
     t->n_lut = (int32_t)(top - base + 1);
     t->n_complex = 0;
     // slot below the first band: the number of edges with c = 0 (0 or 1)
-    const int slot0 = bands.front().k;
+    const int slot0 = bands[0].k;
     for (long long q = base; q <= top; ++q) {
         const uint32_t q_lo = (uint32_t)(q << shift);
         const uint32_t q_hi = (uint32_t)(((q + 1) << shift) - 1);
         int hits = 0, which = -1;
         int slot_before = slot0;
-        for (size_t i = 0; i < bands.size(); ++i) {
+        for (size_t i = 0; i < n_bands; ++i) {
             if (bands[i].hi < q_lo) slot_before = bands[i].k + 1;
             if (bands[i].lo <= q_hi && bands[i].hi >= q_lo) {
                 ++hits;

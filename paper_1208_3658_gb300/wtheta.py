@@ -21,7 +21,8 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "wtheta.h")
 
 WTHETA_OK = 0
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUDGET",
-          -6: "EDEVICE"}
+          -6: "EDEVICE", -7: "ESIZE"}
+NOALLOC_MAX_POINTS, NOALLOC_TILE = 262144, 1024
 BINS_LINEAR, BINS_LN, BINS_LOG10 = 0, 1, 2
 DERR_NONFINITE, DERR_DEC_RANGE, DERR_NOT_UNIT = 1, 2, 4
 STAT_PAIRS, STAT_BINNED, STAT_RECHECK, STAT_TILES, NSTATS = 0, 1, 2, 3, 4
@@ -74,6 +75,7 @@ def lib() -> ctypes.CDLL:
             L.wtheta_ls.argtypes = [u64p, u64p, u64p, i64, i64, i32, dp]
             L.wtheta_ls_cross.argtypes = [u64p, u64p, u64p, u64p, i64, i64, i64, i64, i32, dp]
             L.wtheta_correlate.argtypes = [dp, i64, dp, i64, dp, i32, u64p, dp, vp]
+            L.wtheta_count_xyz_noalloc.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
             L.wtheta_kernel_launches.argtypes = []
             L.wtheta_kernel_launches.restype = ctypes.c_uint64
             _lib = L
@@ -181,6 +183,17 @@ def wtheta_count_xyz(xyz_a, xyz_b, edges_deg, is_auto: bool, counts, stream=None
     _check(lib().wtheta_count_xyz(_dev_ptr(xyz_a), na, _dev_ptr(xyz_b), nb, ep, len(e) - 1,
                                   1 if is_auto else 0, _dev_ptr(counts), _stream(stream)),
            "wtheta_count_xyz")
+
+
+def wtheta_count_xyz_noalloc(xyz_a, xyz_b, edges_deg, is_auto: bool, counts, stream=None):
+    """wtheta_count_xyz without any device allocation: the library's fixed
+    scratch array is used instead (see include/wtheta.h for its limit)."""
+    e, ep = _host_f64(edges_deg)
+    na = _n_points(xyz_a, 3)
+    nb = na if is_auto else _n_points(xyz_b, 3)
+    _check(lib().wtheta_count_xyz_noalloc(_dev_ptr(xyz_a), na, _dev_ptr(xyz_b), nb, ep, len(e) - 1,
+                                          1 if is_auto else 0, _dev_ptr(counts), _stream(stream)),
+           "wtheta_count_xyz_noalloc")
 
 
 def wtheta_count_ex(coords_a, coords_b, coords_are_xyz: bool, edges_deg, is_auto: bool, counts,
