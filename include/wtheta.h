@@ -134,18 +134,22 @@ int wtheta_count_xyz(const double* xyz_a, int64_t n_a, const double* xyz_b,
 
 /* Tuning knobs of the counting kernel; zero fields mean "choose". */
 typedef struct wtheta_tune {
-    int32_t threads;           /* threads per block: 128 or 256              */
-    int32_t points_per_thread; /* A points held in registers per thread: 4 or 8 */
-    int32_t hist_mode;         /* 1: private per-thread histograms (no atomics);
-                                  2: per-warp histograms, warp-aggregated atomics */
-    int32_t reserved;
+    int32_t threads;           /* threads per block: 64, 128 or 256           */
+    int32_t points_per_thread; /* A points held in registers per thread: 8 or 16 */
+    int32_t hist_mode;         /* 1: private per-thread histograms, plain add;
+                                  2: per-warp histograms, warp-aggregated atomics;
+                                  3: private per-thread histograms, shared atomic add */
+    int32_t j_per_screen;      /* B points per screening test: 1 or 2          */
+    int32_t deferred;          /* 1: bin in-range pairs as they are screened;
+                                  2: note screened steps, recompute and bin after */
+    int32_t blocks_per_sm;     /* resident blocks per SM the grid is sized for */
 } wtheta_tune;
 
 /* statistics slots accumulated by wtheta_count_ex (uint64 each) */
-#define WTHETA_STAT_PAIRS 0     /* pairs evaluated, padding included         */
-#define WTHETA_STAT_BINNED 1    /* pairs below the top edge's guard band      */
-#define WTHETA_STAT_RECHECK 2   /* pairs recomputed in FP64                   */
-#define WTHETA_STAT_TILES 3     /* tile pairs processed                       */
+#define WTHETA_STAT_PAIRS 0     /* pairs evaluated, tile padding included     */
+#define WTHETA_STAT_RECHECK 1   /* pairs recomputed in FP64 (guard band)      */
+#define WTHETA_STAT_TILES 2     /* tile pairs evaluated                       */
+#define WTHETA_STAT_SKIPPED 3   /* tile pairs skipped as wholly out of range  */
 #define WTHETA_NSTATS 4
 
 /*

@@ -6,12 +6,18 @@
 // matrix into sub-matrices, one kernel launch each, with per-block shared
 // histograms summed on the host.  Here one persistent launch walks the whole
 // (triangular or rectangular) space of tile pairs from a device work cursor:
-//   - RA/Dec -> FP64 unit vectors once per point (SoA, for the rare FP64
-//     recheck) and FP32 float4 copies (x, y, z, 0) padded to whole tiles with
+//   - RA/Dec -> FP64 unit vectors once per point (kept in the caller's order
+//     for the rare FP64 recheck);
+//   - the points are put in spatial order (cube-map face, then a Hilbert curve
+//     on the face; a counting sort over cells) so that a tile of consecutive
+//     points is a compact patch of sky and a warp's pairs mostly share one
+//     fate (all beyond the top edge, or all in range);
+//   - FP32 float4 copies (x, y, z, original index) padded to whole tiles with
 //     far-away sentinel points that never land in a bin;
-//   - a CTA loads the B tile into shared memory and keeps R A points per
-//     thread in registers; each pair costs 3 FADD + 1 FMUL + 2 FFMA for the
-//     FP32 squared chord s;
+//   - a CTA stages the B tile in shared memory, negated and duplicated for
+//     packed FP32x2 arithmetic, and keeps R A points per thread in registers;
+//     the squared chord of two pairs costs 3 add.f32x2 + 1 mul.f32x2 +
+//     2 fma.f32x2, i.e. the 6 FP32 operations per pair in half the issue slots;
 //   - s is screened against the top edge: pairs beyond it are overflow and
 //     cost nothing more (Sec. 2.2: separations outside the bin range can be
 //     skipped); the overflow slot is filled at the end as total minus the rest;
@@ -48,56 +54,223 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return d;
 }
 
+// two FP32 values packed in one 64-bit register, for the sm_100-family
+// packed FP32x2 instructions (each lane rounds exactly like its scalar op)
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t pack2(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f2_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t add2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t mul2(f2_t a, f2_t b) {
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t fma2(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// Shared-memory accesses of the hot loops, through 32-bit shared-window
+// addresses (so no generic 64-bit address arithmetic on the way).
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void lds_f2x2(unsigned a, f2_t& x, f2_t& y) {
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(x), "=l"(y) : "r"(a));
+}
+__device__ __forceinline__ f2_t lds_f2(unsigned a) {
+    f2_t z;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(z) : "r"(a));
+    return z;
+}
+__device__ __forceinline__ uint4 lds_u4(unsigned a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ void red_add_shared(unsigned a, unsigned v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" :: "r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void inc_shared(unsigned a) {
+    unsigned c;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(c) : "r"(a) : "memory");
+    asm volatile("st.shared.b32 [%0], %1;" :: "r"(a), "r"(c + 1u) : "memory");
+}
+
 // ---------------------------------------------------------------------------
 // conversion kernels
 // ---------------------------------------------------------------------------
-// RA/Dec degrees -> FP64 unit vectors (SoA with stride xyz_stride) and, when
-// p32 is not null, FP32 float4 copies for n <= i < n_pad set to sentinels
-// (sign * kSentinel * (i - n + 1), 0, 0).
-__global__ void k_radec_to_xyz(const double* __restrict__ rd, long long n, long long n_pad,
-                               double* __restrict__ xyz, long long xyz_stride,
-                               float4* __restrict__ p32, float sign) {
+__device__ __forceinline__ void radec_unit(double ra, double dec, double& x, double& y, double& z) {
     const double d2r = 3.14159265358979323846 / 180.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (i < n) {
-            const double ra = rd[2 * i], dec = rd[2 * i + 1];
-            if (!isfinite(ra) || !isfinite(dec)) atomicOr(&g_device_error, WTHETA_DERR_NONFINITE);
-            else if (fabs(dec) > 90.0) atomicOr(&g_device_error, WTHETA_DERR_DEC_RANGE);
-            const double a = ra * d2r, d = dec * d2r;
-            const double cd = cos(d), sd = sin(d), ca = cos(a), sa = sin(a);
-            const double x = __dmul_rn(cd, ca), y = __dmul_rn(cd, sa), z = sd;
-            if (xyz) {
-                xyz[i] = x;
-                xyz[xyz_stride + i] = y;
-                xyz[2 * xyz_stride + i] = z;
-            }
-            if (p32)
-                p32[i] = make_float4(__double2float_rn(x), __double2float_rn(y),
-                                     __double2float_rn(z), 0.f);
-        } else if (p32) {
-            p32[i] = make_float4(sign * kSentinel * (float)(i - n + 1), 0.f, 0.f, 0.f);
-        }
+    if (!isfinite(ra) || !isfinite(dec)) atomicOr(&g_device_error, WTHETA_DERR_NONFINITE);
+    else if (fabs(dec) > 90.0) atomicOr(&g_device_error, WTHETA_DERR_DEC_RANGE);
+    const double a = ra * d2r, d = dec * d2r;
+    const double cd = cos(d), sd = sin(d), ca = cos(a), sa = sin(a);
+    x = __dmul_rn(cd, ca);
+    y = __dmul_rn(cd, sa);
+    z = sd;
+}
+
+__device__ __forceinline__ void check_unit(double x, double y, double z) {
+    if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
+        atomicOr(&g_device_error, WTHETA_DERR_NONFINITE);
+    } else {
+        const double r2 = x * x + y * y + z * z;
+        if (fabs(r2 - 1.0) > 1e-6) atomicOr(&g_device_error, WTHETA_DERR_NOT_UNIT);
     }
 }
 
-// Caller's FP64 SoA unit vectors -> FP32 float4 copies (+ sentinels).
+__device__ __forceinline__ float4 point32(double x, double y, double z, long long idx) {
+    return make_float4(__double2float_rn(x), __double2float_rn(y), __double2float_rn(z),
+                       __int_as_float((int)idx));
+}
+
+__device__ __forceinline__ float4 sentinel32(float sign, long long k) {
+    return make_float4(sign * kSentinel * (float)(k + 1), 0.f, 0.f, 0.f);
+}
+
+// RA/Dec degrees -> FP64 unit vectors (SoA with stride xyz_stride).
+__global__ void k_radec_to_xyz(const double* __restrict__ rd, long long n,
+                               double* __restrict__ xyz, long long xyz_stride) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double x, y, z;
+        radec_unit(rd[2 * i], rd[2 * i + 1], x, y, z);
+        xyz[i] = x;
+        xyz[xyz_stride + i] = y;
+        xyz[2 * xyz_stride + i] = z;
+    }
+}
+
+// Caller's FP64 SoA unit vectors -> FP32 float4 copies in the same order
+// (w = index), then sentinels up to n_pad.
 __global__ void k_xyz_to_f32(const double* __restrict__ xyz, long long n, long long n_pad,
                              float4* __restrict__ p32, float sign) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
          i += (long long)gridDim.x * blockDim.x) {
         if (i < n) {
             const double x = xyz[i], y = xyz[n + i], z = xyz[2 * n + i];
-            if (!isfinite(x) || !isfinite(y) || !isfinite(z)) {
-                atomicOr(&g_device_error, WTHETA_DERR_NONFINITE);
-            } else {
-                const double r2 = x * x + y * y + z * z;
-                if (fabs(r2 - 1.0) > 1e-6) atomicOr(&g_device_error, WTHETA_DERR_NOT_UNIT);
-            }
-            p32[i] = make_float4(__double2float_rn(x), __double2float_rn(y),
-                                 __double2float_rn(z), 0.f);
+            check_unit(x, y, z);
+            p32[i] = point32(x, y, z, i);
         } else {
-            p32[i] = make_float4(sign * kSentinel * (float)(i - n + 1), 0.f, 0.f, 0.f);
+            p32[i] = sentinel32(sign, i - n);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// spatial order: cube-map face + Hilbert index of a 2^L x 2^L grid on it
+// ---------------------------------------------------------------------------
+// Position along the Hilbert curve of cell (x, y) in an S x S grid (S a power
+// of two): descend the quadrants from the largest, adding each quadrant's
+// offset along the curve and reflecting/transposing the remaining coordinates
+// into that quadrant's orientation.
+__device__ __forceinline__ unsigned hilbert_index(unsigned S, unsigned x, unsigned y) {
+    unsigned d = 0;
+    for (unsigned h = S >> 1; h > 0; h >>= 1) {
+        const unsigned rx = (x & h) ? 1u : 0u, ry = (y & h) ? 1u : 0u;
+        d += h * h * ((3u * rx) ^ ry);
+        if (ry == 0) {
+            if (rx == 1) {
+                x = S - 1 - x;
+                y = S - 1 - y;
+            }
+            const unsigned t = x;
+            x = y;
+            y = t;
+        }
+    }
+    return d;
+}
+
+__device__ __forceinline__ unsigned cell_key(double x, double y, double z, int L) {
+    const double ax = fabs(x), ay = fabs(y), az = fabs(z);
+    unsigned face;
+    double u, v, m;
+    if (ax >= ay && ax >= az) { face = x >= 0 ? 0u : 1u; u = y; v = z; m = ax; }
+    else if (ay >= az)        { face = y >= 0 ? 2u : 3u; u = x; v = z; m = ay; }
+    else                      { face = z >= 0 ? 4u : 5u; u = x; v = y; m = az; }
+    const unsigned S = 1u << L;
+    if (!(m > 0.0)) return face * S * S;  // not a unit vector; any cell will do
+    const double fu = (u / m + 1.0) * 0.5 * (double)S, fv = (v / m + 1.0) * 0.5 * (double)S;
+    const unsigned iu = (unsigned)fmin(fmax(fu, 0.0), (double)(S - 1));
+    const unsigned iv = (unsigned)fmin(fmax(fv, 0.0), (double)(S - 1));
+    return face * S * S + hilbert_index(S, iu, iv);
+}
+
+// Cell of every point and the number of points per cell.
+__global__ void k_cell_count(const double* __restrict__ xyz, long long stride, long long n,
+                             int L, int check, unsigned* __restrict__ key,
+                             unsigned* __restrict__ cell_count) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double x = xyz[i], y = xyz[stride + i], z = xyz[2 * stride + i];
+        if (check) check_unit(x, y, z);
+        const unsigned k = cell_key(x, y, z, L);
+        key[i] = k;
+        atomicAdd(cell_count + k, 1u);
+    }
+}
+
+// Exclusive prefix sum of the cell counts, in place (one block of 1024).
+__global__ void __launch_bounds__(1024) k_scan_cells(unsigned* __restrict__ cell, int n_cells) {
+    __shared__ unsigned warp_sum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int per = (n_cells + 1023) / 1024;
+    const int lo = min(t * per, n_cells), hi = min(lo + per, n_cells);
+    unsigned sum = 0;
+    for (int i = lo; i < hi; ++i) sum += cell[i];
+    unsigned incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) warp_sum[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        unsigned ws = warp_sum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned v = __shfl_up_sync(0xffffffffu, ws, o);
+            if (lane >= o) ws += v;
+        }
+        warp_sum[lane] = ws;  // inclusive over warps
+    }
+    __syncthreads();
+    unsigned run = incl - sum + (w > 0 ? warp_sum[w - 1] : 0u);
+    for (int i = lo; i < hi; ++i) {
+        const unsigned c = cell[i];
+        cell[i] = run;
+        run += c;
+    }
+}
+
+// Places every point at its cell's next free slot (FP32 copy, w = original
+// index); slots n..n_pad-1 get sentinels.  Order inside a cell is whatever
+// the atomics give: counts do not depend on it.
+__global__ void k_scatter(const double* __restrict__ xyz, long long stride, long long n,
+                          long long n_pad, const unsigned* __restrict__ key,
+                          unsigned* __restrict__ cell_next, float4* __restrict__ p32, float sign) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (i < n) {
+            const unsigned pos = atomicAdd(cell_next + key[i], 1u);
+            p32[pos] = point32(xyz[i], xyz[stride + i], xyz[2 * stride + i], i);
+        } else {
+            p32[i] = sentinel32(sign, i - n);
         }
     }
 }
@@ -115,13 +288,14 @@ __global__ void k_finalize(unsigned long long* counts, int K, unsigned long long
 // the pair-count kernel
 // ---------------------------------------------------------------------------
 struct PairParams {
-    const float4* a32;
+    const float4* a32;       // FP32 points (x, y, z, original index bits), tile-padded
     const float4* b32;
-    const double* a64;       // FP64 SoA of catalogue a, stride a64_stride
+    const double* a64;       // FP64 SoA in the original order, stride a64_stride
     const double* b64;
     long long a64_stride, b64_stride;
     long long tiles_a, tiles_b;
-    long long n_items;       // tile pairs
+    long long item_begin;    // first tile pair of this launch
+    long long n_items;       // tile pairs of this launch
     int is_auto;
     int items_per_flush;     // flush the uint32 histograms after this many items
     unsigned long long* cursor;
@@ -130,7 +304,12 @@ struct PairParams {
     BinTable tab;
 };
 
-enum HistMode { kHistLane = 1, kHistWarp = 2 };
+// kHistLane: one private uint32 column per thread, plain read-modify-write;
+// kHistWarp: one column per warp, lanes with equal slots merged by
+//            __match_any_sync and added by one shared atomic;
+// kHistLaneAtomic: one private column per thread, updated by a shared atomic
+//            add (one instruction instead of load, add, store).
+enum HistMode { kHistLane = 1, kHistWarp = 2, kHistLaneAtomic = 3 };
 
 // Tile-pair index -> (I, J).  Auto: upper triangle I <= J, row-major.
 __device__ __forceinline__ void item_to_tiles(long long t, long long T_a, long long T_b,
@@ -152,42 +331,46 @@ __device__ __forceinline__ void item_to_tiles(long long t, long long T_a, long l
     *J = i + (t - (i * T - i * (i - 1) / 2));
 }
 
-// FP64 recheck: the definition's squared chord and slot for pair (i, j).
-__device__ __noinline__ unsigned recheck_slot(const double* __restrict__ a64, long long as,
-                                              long long i, const double* __restrict__ b64,
-                                              long long bs, long long j,
-                                              const double* __restrict__ c64, int K) {
-    const double dx = __dsub_rn(a64[i], b64[j]);
-    const double dy = __dsub_rn(a64[as + i], b64[bs + j]);
-    const double dz = __dsub_rn(a64[2 * as + i], b64[2 * bs + j]);
+// FP64 recheck: the definition's squared chord and slot for the pair of
+// sorted positions (ia, jb), found in the caller's FP64 arrays through the
+// original indices kept in the FP32 copies.
+__device__ __forceinline__ unsigned recheck_slot(const PairParams& p, long long ia, long long jb,
+                                                 const double* __restrict__ c64, int K) {
+    const long long i = __float_as_int(p.a32[ia].w);
+    const long long j = __float_as_int(p.b32[jb].w);
+    const double* a = p.a64;
+    const double* b = p.b64;
+    const long long as = p.a64_stride, bs = p.b64_stride;
+    const double dx = __dsub_rn(a[i], b[j]);
+    const double dy = __dsub_rn(a[as + i], b[bs + j]);
+    const double dz = __dsub_rn(a[2 * as + i], b[2 * bs + j]);
     const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     unsigned k = 0;
     while (k <= (unsigned)K && c64[k] <= s) ++k;
     return k;  // K+1 = overflow
 }
 
-template <int NT, int R, int HM>
+template <int NT, int R, int JU, int HM, int DEF>
 struct PairKernel {
     static constexpr int TA = NT * R;   // A points per tile
     static constexpr int TB = NT * R;   // B points per tile (equal: auto needs square tiles)
     static constexpr int NW = NT / 32;
-    static constexpr int HCOLS = HM == kHistLane ? NT : NW;
+    static constexpr int HCOLS = HM == kHistWarp ? NW : NT;
 
     static size_t smem_bytes(int K, int n_lut) {
-        size_t b = (size_t)TB * 16;             // B tile
+        size_t b = (size_t)TB * 24;             // B tile: {-x,-x,-y,-y} + {-z,-z}
         b += (size_t)n_lut * 16;                // screening table
         b += (size_t)(K + 2) * 8;               // FP64 edges (+ pad)
-        b += (size_t)(K + 1) * HCOLS * 4;       // histograms
+        b += (size_t)(K + 2) * HCOLS * 4;       // histograms, row K+1 a trash row
         return b;
     }
 };
 
-template <int NT, int R, int HM>
+template <int NT, int HCOLS>
 __device__ __forceinline__ void flush_hist(unsigned* hist, int K,
                                            unsigned long long* __restrict__ counts) {
-    constexpr int HCOLS = PairKernel<NT, R, HM>::HCOLS;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int b = warp; b <= K; b += NT / 32) {
+    for (int b = warp; b <= K + 1; b += NT / 32) {
         unsigned long long sum = 0;
         for (int q = lane; q < HCOLS; q += 32) {
             sum += hist[b * HCOLS + q];
@@ -195,159 +378,255 @@ __device__ __forceinline__ void flush_hist(unsigned* hist, int K,
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0 && sum) atomicAdd(counts + b, sum);
+        if (lane == 0 && sum && b <= K) atomicAdd(counts + b, sum);  // row K+1 is trash
     }
 }
 
-// One tile pair: B tile in shared memory, R A points per thread in registers.
-template <int NT, int R, int HM, bool DIAG>
-__device__ __forceinline__ void tile_pass(const float4* __restrict__ sB, const uint4* __restrict__ sLut,
-                                          const double* __restrict__ sC, unsigned* __restrict__ hist,
-                                          const float (&ax)[R], const float (&ay)[R],
-                                          const float (&az)[R], const PairParams& p,
-                                          long long I, long long J, unsigned long long& n_binned,
-                                          unsigned long long& n_recheck) {
-    constexpr int TA = PairKernel<NT, R, HM>::TA;
-    constexpr int TB = PairKernel<NT, R, HM>::TB;
-    constexpr int HCOLS = PairKernel<NT, R, HM>::HCOLS;
+// Byte offset of the histogram row of an FP32 squared chord.  The table
+// gives the row below / above the guard band of the bucket's edge; values
+// beyond the top edge (or masked with +inf) get the trash row K+1.  A value
+// inside a guard band also goes to the trash row and sets *amb: the caller
+// recounts it after an FP64 recheck.  No branch.
+__device__ __forceinline__ unsigned row_offset(unsigned bits, unsigned lut, int shift, int base,
+                                               int top_idx, unsigned h_top, unsigned trash,
+                                               bool* amb) {
+    const int idx = min(max((int)(bits >> shift) - base, 0), top_idx);
+    const uint4 e = lds_u4(lut + 16u * (unsigned)idx);
+    const bool in_band = bits >= e.x && bits <= e.y && bits <= h_top;
+    *amb = in_band;
+    return in_band ? trash : (bits < e.x ? e.z : e.w);
+}
+
+template <int HM>
+__device__ __forceinline__ void hist_inc(unsigned cell) {
+    if (HM == kHistLane) inc_shared(cell);
+    else red_add_shared(cell, 1u);
+}
+
+// Bins NV screened values s[h R + r] (pairs of A point r and B point j + h)
+// into the thread's private histogram column at shared address col.
+template <int NT, int R, int NV, int HM>
+__device__ __forceinline__ void bin_values(const float (&s)[NV], unsigned col, unsigned lut,
+                                           int shift, int base, int top_idx, unsigned h_top,
+                                           unsigned row_bytes, int K, const PairParams& p,
+                                           long long a0, long long bj,
+                                           const double* __restrict__ sC,
+                                           unsigned long long& n_recheck) {
+    const unsigned trash = (unsigned)(K + 1) * row_bytes;
+    unsigned amb_mask = 0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        bool amb;
+        const unsigned off = row_offset(__float_as_uint(s[v]), lut, shift, base, top_idx, h_top,
+                                        trash, &amb);
+        amb_mask |= amb ? (1u << v) : 0u;
+        hist_inc<HM>(col + off);
+    }
+    // rare: values inside a guard band, recomputed in FP64 (one copy of the code)
+    while (amb_mask) {
+        const int v = __ffs(amb_mask) - 1;
+        amb_mask &= amb_mask - 1;
+        const unsigned slot = recheck_slot(p, a0 + (v % R) * NT, bj + v / R, sC, K);
+        ++n_recheck;
+        hist_inc<HM>(col + slot * row_bytes);
+    }
+}
+
+// Squared chords of JU consecutive B points (from j) with the thread's R A
+// points: s[h R + r].  On a diagonal tile, pairs with i >= j get +inf.  The
+// B tile sits at shared addresses bxy (16 B per point: -x,-x,-y,-y) and
+// bz (8 B per point: -z,-z).
+template <int NT, int R, int JU, bool DIAG>
+__device__ __forceinline__ void chords(float (&s)[JU * R], unsigned bxy_base, unsigned bz_base,
+                                       const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
+                                       const f2_t (&az)[R / 2], int j) {
+#pragma unroll
+    for (int h = 0; h < JU; ++h) {
+        f2_t bx, by;
+        lds_f2x2(bxy_base + 16u * (unsigned)(j + h), bx, by);
+        const f2_t bz = lds_f2(bz_base + 8u * (unsigned)(j + h));
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) {
+            const f2_t dx = add2(ax[q], bx);
+            const f2_t dy = add2(ay[q], by);
+            const f2_t dz = add2(az[q], bz);
+            const f2_t t = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+            unpack2(t, s[h * R + 2 * q], s[h * R + 2 * q + 1]);
+        }
+    }
+    if (DIAG) {
+#pragma unroll
+        for (int h = 0; h < JU; ++h)
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (j + h <= r * NT + (int)threadIdx.x) s[h * R + r] = __int_as_float(0x7f800000);
+    }
+}
+
+template <int NV>
+__device__ __forceinline__ float min_of(const float (&s)[NV]) {
+    float m = s[0];
+#pragma unroll
+    for (int v = 1; v + 1 < NV; v += 2) m = min3f(m, s[v], s[v + 1]);
+    if (NV % 2 == 0) m = fminf(m, s[NV - 1]);
+    return m;
+}
+
+template <int NT, int R, int JU, int HM, int DEF, bool DIAG>
+__device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lut,
+                                          const double* __restrict__ sC, unsigned hist,
+                                          const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
+                                          const f2_t (&az)[R / 2], const PairParams& p,
+                                          long long I, long long J, unsigned long long& n_recheck) {
+    using PK = PairKernel<NT, R, JU, HM, DEF>;
+    constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
+    constexpr int NV = JU * R;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float hf = __uint_as_float(p.tab.h_top);
-    const int shift = p.tab.shift, base = p.tab.base, K = p.tab.K;
-    unsigned* myhist = HM == kHistLane ? hist + tid : hist + warp;
+    const unsigned h_top = p.tab.h_top;
+    const float hf = __uint_as_float(h_top);
+    const int shift = p.tab.shift, base = p.tab.base, K = p.tab.K, top_idx = p.tab.n_lut - 1;
+    const unsigned row_bytes = HCOLS * 4u;
+    const unsigned col = hist + 4u * (unsigned)(HM == kHistWarp ? warp : tid);
+    const long long a0 = I * TA + tid, b0 = J * TB;
 
-#pragma unroll 2
-    for (int j = 0; j < TB; ++j) {
-        const float4 b = sB[j];
-        float s[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float dx = ax[r] - b.x, dy = ay[r] - b.y, dz = az[r] - b.z;
-            s[r] = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-            if (DIAG) {
-                if (j <= r * NT + tid) s[r] = __int_as_float(0x7f800000);  // i >= j: not a pair
+    if (DEF) {
+        // Deferred binning: the screening loop only notes, one bit per step,
+        // which of 32 consecutive steps hold an in-range value; those steps
+        // are then recomputed and binned.  The screening loop stays small.
+        static_assert(TB % (32 * JU) == 0, "tile must hold whole 32-step blocks");
+#pragma unroll 1
+        for (int jb = 0; jb < TB; jb += 32 * JU) {
+            unsigned mask = 0;
+#pragma unroll 1
+            for (int st = 0; st < 32; ++st) {
+                float s[NV];
+                chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, jb + st * JU);
+                mask |= (min_of(s) <= hf ? 1u : 0u) << st;
+            }
+            while (mask) {
+                const int st = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int j = jb + st * JU;
+                float s[NV];
+                chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
+                bin_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx, h_top, row_bytes, K,
+                                          p, a0, b0 + j, sC, n_recheck);
             }
         }
-        float m = s[0];
-#pragma unroll
-        for (int r = 1; r + 1 < R; r += 2) m = min3f(m, s[r], s[r + 1]);
-        if (R % 2 == 0) m = fminf(m, s[R - 1]);
+        return;
+    } else {
+#pragma unroll 1
+    for (int j = 0; j < TB; j += JU) {
+        float s[NV];
+        chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
+        const float m = min_of(s);
 
-        const bool any_in = m <= hf;
-        if (HM == kHistLane) {
-            if (!any_in) continue;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (s[r] <= hf) {
-                    const unsigned bits = __float_as_uint(s[r]);
-                    const int idx = max((int)(bits >> shift) - base, 0);
-                    const uint4 e = sLut[idx];
-                    unsigned slot;
-                    if (bits < e.x) slot = e.z;
-                    else if (bits > e.y) slot = e.w;
-                    else {
-                        slot = recheck_slot(p.a64, p.a64_stride, I * TA + r * NT + tid, p.b64,
-                                            p.b64_stride, J * TB + j, sC, K);
-                        ++n_recheck;
-                    }
-                    if (slot <= (unsigned)K) myhist[slot * HCOLS] += 1u;
-                    ++n_binned;
-                }
-            }
+        if (HM != kHistWarp) {
+            if (!(m <= hf)) continue;
+            bin_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx, h_top, row_bytes, K, p,
+                                      a0, b0 + j, sC, n_recheck);
         } else {
-            if (!__any_sync(0xffffffffu, any_in)) continue;
+            if (!__any_sync(0xffffffffu, m <= hf)) continue;
+            const unsigned trash = (unsigned)(K + 1) * row_bytes;
+            unsigned amb_mask = 0;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const bool in = s[r] <= hf;
-                unsigned slot = 0xffffffffu;
-                if (in) {
-                    const unsigned bits = __float_as_uint(s[r]);
-                    const int idx = max((int)(bits >> shift) - base, 0);
-                    const uint4 e = sLut[idx];
-                    if (bits < e.x) slot = e.z;
-                    else if (bits > e.y) slot = e.w;
-                    else {
-                        slot = recheck_slot(p.a64, p.a64_stride, I * TA + r * NT + tid, p.b64,
-                                            p.b64_stride, J * TB + j, sC, K);
-                        ++n_recheck;
-                    }
-                    ++n_binned;
-                }
-                const bool take = in && slot <= (unsigned)K;
-                const unsigned act = __ballot_sync(0xffffffffu, take);
-                if (take) {
-                    const unsigned peers = __match_any_sync(act, slot);
-                    if (lane == __ffs(peers) - 1)
-                        atomicAdd(myhist + slot * HCOLS, (unsigned)__popc(peers));
-                }
+            for (int v = 0; v < NV; ++v) {
+                bool amb;
+                const unsigned off = row_offset(__float_as_uint(s[v]), lut, shift, base, top_idx,
+                                                h_top, trash, &amb);
+                amb_mask |= amb ? (1u << v) : 0u;
+                const unsigned peers = __match_any_sync(0xffffffffu, off);
+                if (lane == __ffs(peers) - 1) red_add_shared(col + off, (unsigned)__popc(peers));
+            }
+            while (amb_mask) {
+                const int v = __ffs(amb_mask) - 1;
+                amb_mask &= amb_mask - 1;
+                const unsigned slot = recheck_slot(p, a0 + (v % R) * NT, b0 + j + v / R, sC, K);
+                ++n_recheck;
+                red_add_shared(col + slot * row_bytes, 1u);
             }
         }
     }
-    (void)lane;
+    }
 }
 
-template <int NT, int R, int HM>
+template <int NT, int R, int JU, int HM, int DEF>
 __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams p) {
-    using PK = PairKernel<NT, R, HM>;
+    using PK = PairKernel<NT, R, JU, HM, DEF>;
     constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.tab.K;
-    float4* sB = reinterpret_cast<float4*>(smem);
-    uint4* sLut = reinterpret_cast<uint4*>(sB + TB);
+    ulonglong2* sBxy = reinterpret_cast<ulonglong2*>(smem);
+    f2_t* sBz = reinterpret_cast<f2_t*>(sBxy + TB);
+    uint4* sLut = reinterpret_cast<uint4*>(sBz + TB);
     double* sC = reinterpret_cast<double*>(sLut + p.tab.n_lut);
     unsigned* hist = reinterpret_cast<unsigned*>(sC + (K + 2));
     __shared__ long long s_item;
 
     const int tid = threadIdx.x;
+    const unsigned row_bytes = HCOLS * 4u;
     for (int q = tid; q < p.tab.n_lut; q += NT)
-        sLut[q] = make_uint4(p.tab.lut[q][0], p.tab.lut[q][1], p.tab.lut[q][2], p.tab.lut[q][3]);
+        sLut[q] = make_uint4(p.tab.lut[q][0], p.tab.lut[q][1], p.tab.lut[q][2] * row_bytes,
+                             p.tab.lut[q][3] * row_bytes);
     for (int q = tid; q <= K; q += NT) sC[q] = p.tab.c64[q];
-    for (int q = tid; q < (K + 1) * HCOLS; q += NT) hist[q] = 0u;
+    for (int q = tid; q < (K + 2) * HCOLS; q += NT) hist[q] = 0u;
 
-    unsigned long long n_binned = 0, n_recheck = 0, n_items = 0;
+    unsigned long long n_recheck = 0, n_items = 0;
     int since_flush = 0;
     for (;;) {
         if (tid == 0) s_item = (long long)atomicAdd(p.cursor, 1ull);
-        __syncthreads();  // s_item visible; previous item's sB reads finished
+        __syncthreads();  // s_item visible; previous item's shared reads finished
         const long long t = s_item;
         if (t >= p.n_items) break;
         long long I, J;
-        item_to_tiles(t, p.tiles_a, p.tiles_b, p.is_auto, &I, &J);
+        item_to_tiles(p.item_begin + t, p.tiles_a, p.tiles_b, p.is_auto, &I, &J);
         const float4* gB = p.b32 + J * TB;
-#pragma unroll
-        for (int q = 0; q < R; ++q) sB[q * NT + tid] = gB[q * NT + tid];
-        float ax[R], ay[R], az[R];
+#pragma unroll 4
+        for (int q = 0; q < R; ++q) {
+            const float4 b = gB[q * NT + tid];
+            sBxy[q * NT + tid] = make_ulonglong2(pack2(-b.x, -b.x), pack2(-b.y, -b.y));
+            sBz[q * NT + tid] = pack2(-b.z, -b.z);
+        }
+        // The A points are packed two by two for the FP32x2 instructions.
+        // Each value goes through an explicit add of +0 (exact; it only turns
+        // -0 into +0, which leaves every squared chord unchanged): the packed
+        // operands then get registers of their own instead of being formed in
+        // place from the vector-load destinations, a layout measured to cost
+        // about a quarter of the screening loop's throughput.
+        f2_t ax[R / 2], ay[R / 2], az[R / 2];
         const float4* gA = p.a32 + I * TA;
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float4 a = gA[r * NT + tid];
-            ax[r] = a.x; ay[r] = a.y; az[r] = a.z;
+        for (int q = 0; q < R / 2; ++q) {
+            const float4 u = gA[(2 * q) * NT + tid];
+            const float4 v = gA[(2 * q + 1) * NT + tid];
+            ax[q] = pack2(__fadd_rn(u.x, 0.f), __fadd_rn(v.x, 0.f));
+            ay[q] = pack2(__fadd_rn(u.y, 0.f), __fadd_rn(v.y, 0.f));
+            az[q] = pack2(__fadd_rn(u.z, 0.f), __fadd_rn(v.z, 0.f));
         }
         __syncthreads();  // B tile staged
+        const unsigned a_bxy = smem_addr(sBxy), a_bz = smem_addr(sBz), a_lut = smem_addr(sLut),
+                       a_hist = smem_addr(hist);
         if (p.is_auto && I == J)
-            tile_pass<NT, R, HM, true>(sB, sLut, sC, hist, ax, ay, az, p, I, J, n_binned, n_recheck);
+            tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, sC, a_hist, ax, ay, az, p, I,
+                                                J, n_recheck);
         else
-            tile_pass<NT, R, HM, false>(sB, sLut, sC, hist, ax, ay, az, p, I, J, n_binned, n_recheck);
+            tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, sC, a_hist, ax, ay, az, p, I,
+                                                 J, n_recheck);
         ++n_items;
         if (++since_flush == p.items_per_flush) {
             __syncthreads();
-            flush_hist<NT, R, HM>(hist, K, p.counts);
+            flush_hist<NT, HCOLS>(hist, K, p.counts);
             __syncthreads();
             since_flush = 0;
         }
     }
     // all threads left the loop after the same barrier
-    flush_hist<NT, R, HM>(hist, K, p.counts);
+    flush_hist<NT, HCOLS>(hist, K, p.counts);
     if (p.stats) {
-        unsigned long long v1 = n_binned, v2 = n_recheck;
+        unsigned long long v = n_recheck;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            v1 += __shfl_xor_sync(0xffffffffu, v1, o);
-            v2 += __shfl_xor_sync(0xffffffffu, v2, o);
-        }
-        if ((tid & 31) == 0) {
-            if (v1) atomicAdd(p.stats + WTHETA_STAT_BINNED, v1);
-            if (v2) atomicAdd(p.stats + WTHETA_STAT_RECHECK, v2);
-        }
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0 && v) atomicAdd(p.stats + WTHETA_STAT_RECHECK, v);
         if (tid == 0 && n_items) {
             atomicAdd(p.stats + WTHETA_STAT_TILES, n_items);
             atomicAdd(p.stats + WTHETA_STAT_PAIRS, n_items * (unsigned long long)TA * TB);
@@ -359,22 +638,26 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
 // launch plumbing
 // ---------------------------------------------------------------------------
 struct Variant {
-    int nt, r, hm;
+    int nt, r, ju, hm, def;
     void (*kernel)(PairParams);
     size_t (*smem)(int, int);
 };
 
-template <int NT, int R, int HM>
+template <int NT, int R, int JU, int HM, int DEF>
 static Variant make_variant() {
-    return Variant{NT, R, HM, &k_pairs<NT, R, HM>, &PairKernel<NT, R, HM>::smem_bytes};
+    return Variant{NT, R, JU, HM, DEF, &k_pairs<NT, R, JU, HM, DEF>,
+                   &PairKernel<NT, R, JU, HM, DEF>::smem_bytes};
 }
 
+// Instantiated shapes (tile = threads x points_per_thread).  Per-warp
+// histograms (mode 2) need the whole warp in step, so they bin inline.
 static const Variant* variants(int* n) {
     static const Variant v[] = {
-        make_variant<128, 8, kHistLane>(), make_variant<256, 4, kHistLane>(),
-        make_variant<128, 4, kHistLane>(), make_variant<256, 8, kHistLane>(),
-        make_variant<128, 8, kHistWarp>(), make_variant<256, 4, kHistWarp>(),
-        make_variant<128, 4, kHistWarp>(), make_variant<256, 8, kHistWarp>(),
+        make_variant<128, 8, 2, kHistLaneAtomic, 0>(), make_variant<128, 8, 2, kHistLaneAtomic, 1>(),
+        make_variant<128, 8, 2, kHistLane, 1>(),       make_variant<128, 8, 2, kHistWarp, 0>(),
+        make_variant<128, 8, 1, kHistLaneAtomic, 1>(), make_variant<64, 16, 2, kHistLaneAtomic, 1>(),
+        make_variant<64, 16, 2, kHistWarp, 0>(),       make_variant<128, 16, 2, kHistLaneAtomic, 1>(),
+        make_variant<256, 8, 2, kHistLaneAtomic, 1>(), make_variant<256, 8, 2, kHistWarp, 0>(),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;
@@ -413,22 +696,32 @@ static const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, in
     const Variant* v = variants(&nv);
     const int want_nt = tune && tune->threads ? tune->threads : 128;
     const int want_r = tune && tune->points_per_thread ? tune->points_per_thread : 8;
+    const int want_ju = tune && tune->j_per_screen ? tune->j_per_screen : 2;
     int want_hm = tune && tune->hist_mode ? tune->hist_mode : 0;
+    int want_def = tune && tune->deferred ? (tune->deferred == 2 ? 1 : 0) : -1;
+    auto fits = [&](const Variant& x) { return x.smem(K, n_lut) <= (size_t)max_smem; };
+    auto shape = [&](const Variant& x) {
+        return x.nt == want_nt && x.r == want_r && x.ju == want_ju;
+    };
     if (want_hm == 0) {
         // private per-thread histograms while they fit comfortably
-        want_hm = v[0].smem(K, n_lut) <= 100 * 1024 ? kHistLane : kHistWarp;
+        want_hm = kHistWarp;
+        for (int i = 0; i < nv; ++i)
+            if (shape(v[i]) && v[i].hm == kHistLaneAtomic && v[i].smem(K, n_lut) <= 100 * 1024)
+                want_hm = kHistLaneAtomic;
     }
+    if (want_def < 0) want_def = 0;  // inline binning measured faster once in-range pairs matter
     for (int i = 0; i < nv; ++i)
-        if (v[i].nt == want_nt && v[i].r == want_r && v[i].hm == want_hm &&
-            v[i].smem(K, n_lut) <= (size_t)max_smem)
+        if (shape(v[i]) && v[i].hm == want_hm && v[i].def == want_def && fits(v[i])) return &v[i];
+    // fall back: same tile size, per-warp histograms
+    for (int i = 0; i < nv; ++i)
+        if (v[i].nt * v[i].r == want_nt * want_r && v[i].hm == kHistWarp && fits(v[i]))
             return &v[i];
-    // fall back: anything that fits, per-warp first
-    for (int i = 0; i < nv; ++i)
-        if (v[i].hm == kHistWarp && v[i].smem(K, n_lut) <= (size_t)max_smem) return &v[i];
     return nullptr;
 }
 
-static int grid_for(const Variant* v, size_t smem, long long n_items, int sm_count, int* grid) {
+static int grid_for(const Variant* v, size_t smem, long long n_items, int sm_count, int want_per_sm,
+                    int* grid) {
     static std::mutex mu;
     {
         std::lock_guard<std::mutex> g(mu);
@@ -441,6 +734,7 @@ static int grid_for(const Variant* v, size_t smem, long long n_items, int sm_cou
                                                       smem) != cudaSuccess)
         return WTHETA_ECUDA;
     per_sm = std::max(per_sm, 1);
+    if (want_per_sm > 0) per_sm = std::min(per_sm, want_per_sm);
     long long g = (long long)per_sm * sm_count;
     if (g > n_items) g = n_items;
     *grid = (int)std::max(g, 1LL);
@@ -453,6 +747,93 @@ static int check_cuda(cudaError_t e) {
     if (e == cudaSuccess) return WTHETA_OK;
     if (e == cudaErrorMemoryAllocation) return WTHETA_ENOMEM;
     return WTHETA_ECUDA;
+}
+
+static int launch_grid(long long n, int sm_count) {
+    const long long g = (n + 255) / 256;
+    return (int)std::min<long long>(std::max<long long>(g, 1), (long long)sm_count * 16);
+}
+
+// Cell level of the spatial sort: about 4 or more points per cell on
+// average over the sphere, at most 6 * 4^9 cells.
+static int sort_level(long long n) {
+    int L = 1;
+    while (L < 9 && 6LL * (1LL << (2 * (L + 1))) * 4 <= n) ++L;
+    return L;
+}
+
+// One catalogue made ready for the pair kernel: FP64 unit vectors (the
+// caller's, or converted from RA/Dec into scratch) and spatially ordered FP32
+// copies padded to whole tiles.
+struct Prepared {
+    const float4* p32 = nullptr;
+    const double* x64 = nullptr;
+    long long stride = 0;
+};
+
+static size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
+    const int L = sort_level(n);
+    const size_t cells = 6ull << (2 * L);
+    size_t b = (size_t)n_pad * 16 + 256;           // FP32 points
+    b += ((size_t)n * 4 + 255) / 256 * 256;        // cell keys
+    b += (cells * 4 + 255) / 256 * 256;            // cell counts
+    if (!is_xyz) b += ((size_t)n * 24 + 255) / 256 * 256;  // FP64 SoA
+    return b;
+}
+
+static int prepare(const double* coords, long long n, long long n_pad, int is_xyz, float sign,
+                   unsigned char* scratch, int sm_count, cudaStream_t st, Prepared* out) {
+    const int L = sort_level(n);
+    const int cells = 6 << (2 * L);
+    unsigned char* sp = scratch;
+    float4* p32 = (float4*)sp;
+    sp += ((size_t)n_pad * 16 + 255) / 256 * 256;
+    unsigned* key = (unsigned*)sp;
+    sp += ((size_t)n * 4 + 255) / 256 * 256;
+    unsigned* cell = (unsigned*)sp;
+    sp += ((size_t)cells * 4 + 255) / 256 * 256;
+    const double* x64 = coords;
+    long long stride = n;
+    if (!is_xyz) {
+        double* x = (double*)sp;
+        k_radec_to_xyz<<<launch_grid(n, sm_count), 256, 0, st>>>(coords, n, x, n);
+        count_launch();
+        x64 = x;
+    }
+    int rc = check_cuda(cudaMemsetAsync(cell, 0, (size_t)cells * 4, st));
+    if (rc) return rc;
+    k_cell_count<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, L, is_xyz, key, cell);
+    k_scan_cells<<<1, 1024, 0, st>>>(cell, cells);
+    k_scatter<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(x64, stride, n, n_pad, key, cell, p32,
+                                                            sign);
+    count_launch(3);
+    out->p32 = p32;
+    out->x64 = x64;
+    out->stride = stride;
+    return check_cuda(cudaGetLastError());
+}
+
+static PairParams make_params(const Variant* v, const BinTable& tab, const Prepared& A,
+                              const Prepared& B, long long ta, long long tb, int is_auto,
+                              long long item_begin, long long n_items,
+                              unsigned long long* cursor, unsigned long long* counts,
+                              unsigned long long* stats) {
+    PairParams prm;
+    std::memset(&prm, 0, sizeof(prm));
+    prm.a32 = A.p32; prm.b32 = B.p32; prm.a64 = A.x64; prm.b64 = B.x64;
+    prm.a64_stride = A.stride; prm.b64_stride = B.stride;
+    prm.tiles_a = ta; prm.tiles_b = tb;
+    prm.item_begin = item_begin; prm.n_items = n_items;
+    prm.is_auto = is_auto;
+    // a thread evaluates R x TB pairs per item, so a histogram cell gains at
+    // most R TB (private per-thread column) or 32 R TB (per-warp column)
+    const unsigned long long per_item = (v->hm == kHistWarp ? 32ull : 1ull) *
+                                        (unsigned long long)v->r * (unsigned long long)v->nt *
+                                        (unsigned long long)v->r;
+    prm.items_per_flush = (int)std::min<unsigned long long>(0xFFFFFFFFull / per_item, 1ull << 30);
+    prm.cursor = cursor; prm.counts = counts; prm.stats = stats;
+    std::memcpy(&prm.tab, &tab, sizeof(tab));
+    return prm;
 }
 
 // Core of wtheta_count / wtheta_count_xyz / wtheta_count_ex.
@@ -472,10 +853,9 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     } else if (n_b > 0 && !cb) {
         return WTHETA_EINVAL;
     }
-    if (tune && ((tune->threads && tune->threads != 128 && tune->threads != 256) ||
-                 (tune->points_per_thread && tune->points_per_thread != 4 &&
-                  tune->points_per_thread != 8) ||
-                 (tune->hist_mode < 0 || tune->hist_mode > 2)))
+    if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
+                 tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
+                 tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0))
         return WTHETA_EINVAL;
     static thread_local BinTable tab;  // large; built per call on the host
     int rc = build_table(edges, K, &tab);
@@ -496,73 +876,32 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     }
 
     const Variant* v = pick_variant(tune, K, tab.n_lut, di.max_smem_optin);
-    if (!v) return WTHETA_EINVAL;
+    if (!v) return WTHETA_EINVAL;  // no instantiated shape matches the tuning request
     const long long T = (long long)v->nt * v->r;  // TA == TB
     const long long pa = round_up(n_a, T), pb = is_auto ? pa : round_up(n_b, T);
 
-    // scratch: FP32 copies of both catalogues, FP64 SoA when converting from
-    // RA/Dec, and the work cursor
-    size_t bytes = (size_t)pa * 16 + (is_auto ? 0 : (size_t)pb * 16) + 256;
-    if (!is_xyz) bytes += (size_t)pa * 24 + (is_auto ? 0 : (size_t)pb * 24);
+    // scratch: the cursor, then each catalogue's prepared copies
+    const size_t ba = prepare_bytes(n_a, pa, is_xyz);
+    const size_t bb = is_auto ? 0 : prepare_bytes(n_b, pb, is_xyz);
     void* scratch = nullptr;
-    if ((rc = check_cuda(cudaMallocAsync(&scratch, bytes, st)))) return rc;
+    if ((rc = check_cuda(cudaMallocAsync(&scratch, 256 + ba + bb, st)))) return rc;
     unsigned char* sp = (unsigned char*)scratch;
     unsigned long long* cursor = (unsigned long long*)sp;
-    sp += 256;
-    float4* a32 = (float4*)sp;
-    sp += (size_t)pa * 16;
-    float4* b32 = a32;
-    if (!is_auto) { b32 = (float4*)sp; sp += (size_t)pb * 16; }
-    const double* a64 = ca;
-    const double* b64 = cb;
-    long long as = n_a, bs = n_b;
-    const int cvt_threads = 256;
-    auto cvt_grid = [&](long long n) {
-        long long g = (n + cvt_threads - 1) / cvt_threads;
-        return (int)std::min<long long>(std::max<long long>(g, 1), (long long)di.sm_count * 16);
-    };
-    if (!is_xyz) {
-        double* x64a = (double*)sp;
-        sp += (size_t)pa * 24;
-        k_radec_to_xyz<<<cvt_grid(pa), cvt_threads, 0, st>>>(ca, n_a, pa, x64a, pa, a32, 1.f);
-        count_launch();
-        a64 = x64a; as = pa;
-        if (!is_auto) {
-            double* x64b = (double*)sp;
-            sp += (size_t)pb * 24;
-            k_radec_to_xyz<<<cvt_grid(pb), cvt_threads, 0, st>>>(cb, n_b, pb, x64b, pb, b32, -1.f);
-            count_launch();
-            b64 = x64b; bs = pb;
-        } else {
-            b64 = a64; bs = as;
-        }
-    } else {
-        k_xyz_to_f32<<<cvt_grid(pa), cvt_threads, 0, st>>>(ca, n_a, pa, a32, 1.f);
-        count_launch();
-        if (!is_auto) {
-            k_xyz_to_f32<<<cvt_grid(pb), cvt_threads, 0, st>>>(cb, n_b, pb, b32, -1.f);
-            count_launch();
-        }
-    }
-    rc = check_cuda(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st));
+    Prepared A, B;
+    rc = prepare(ca, n_a, pa, is_xyz, 1.f, sp + 256, di.sm_count, st, &A);
+    if (!rc && !is_auto) rc = prepare(cb, n_b, pb, is_xyz, -1.f, sp + 256 + ba, di.sm_count, st, &B);
+    if (is_auto) B = A;
+    if (!rc) rc = check_cuda(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st));
 
     const long long ta = pa / T, tb = pb / T;
     const long long n_items = is_auto ? ta * (ta + 1) / 2 : ta * tb;
     const size_t smem = v->smem(K, tab.n_lut);
     int grid = 0;
-    if (!rc) rc = grid_for(v, smem, n_items, di.sm_count, &grid);
+    const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
+    if (!rc) rc = grid_for(v, smem, n_items, di.sm_count, want_per_sm, &grid);
     if (!rc) {
-        PairParams prm;
-        std::memset(&prm, 0, sizeof(prm));
-        prm.a32 = a32; prm.b32 = b32; prm.a64 = a64; prm.b64 = b64;
-        prm.a64_stride = as; prm.b64_stride = bs;
-        prm.tiles_a = ta; prm.tiles_b = tb; prm.n_items = n_items;
-        prm.is_auto = is_auto;
-        // a histogram cell gains at most T (per-thread) or 32 T (per-warp) per item
-        const unsigned long long per_item = (v->hm == kHistLane ? 1ull : 32ull) * (unsigned long long)T;
-        prm.items_per_flush = (int)std::min<unsigned long long>(0xFFFFFFFFull / per_item, 1ull << 30);
-        prm.cursor = cursor; prm.counts = counts; prm.stats = stats;
-        std::memcpy(&prm.tab, &tab, sizeof(tab));
+        const PairParams prm = make_params(v, tab, A, B, ta, tb, is_auto, 0, n_items, cursor,
+                                           counts, stats);
         v->kernel<<<grid, v->nt, smem, st>>>(prm);
         count_launch();
         rc = check_cuda(cudaGetLastError());
@@ -641,7 +980,7 @@ static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double*
         count_launch();
         return check_cuda(cudaGetLastError());
     }
-    wtheta_tune fixed = {128, 8, 0, 0};  // the tile of WTHETA_NOALLOC_TILE points
+    wtheta_tune fixed = {128, 8, 0, 0, 0, 0};  // the tile of WTHETA_NOALLOC_TILE points
     const Variant* v = pick_variant(&fixed, K, tab.n_lut, di.max_smem_optin);
     if (!v || (long long)v->nt * v->r != T) return WTHETA_EINVAL;
 
@@ -665,14 +1004,15 @@ static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double*
     const long long n_items = is_auto ? ta * (ta + 1) / 2 : ta * tb;
     const size_t smem = v->smem(K, tab.n_lut);
     int grid = 0;
-    if ((rc = grid_for(v, smem, n_items, di.sm_count, &grid))) return rc;
+    if ((rc = grid_for(v, smem, n_items, di.sm_count, 0, &grid))) return rc;
     PairParams prm;
     std::memset(&prm, 0, sizeof(prm));
     prm.a32 = a32; prm.b32 = b32; prm.a64 = ca; prm.b64 = cb;
     prm.a64_stride = n_a; prm.b64_stride = n_b;
     prm.tiles_a = ta; prm.tiles_b = tb; prm.n_items = n_items;
     prm.is_auto = is_auto;
-    const unsigned long long per_item = (v->hm == kHistLane ? 1ull : 32ull) * (unsigned long long)T;
+    const unsigned long long per_item = (v->hm == kHistWarp ? 32ull : 1ull) *
+                                        (unsigned long long)v->r * (unsigned long long)T;
     prm.items_per_flush = (int)std::min<unsigned long long>(0xFFFFFFFFull / per_item, 1ull << 30);
     prm.cursor = cursor; prm.counts = counts; prm.stats = nullptr;
     std::memcpy(&prm.tab, &tab, sizeof(tab));
@@ -715,7 +1055,7 @@ int wtheta_radec_to_xyz(const double* rd, int64_t n, double* xyz, void* stream) 
     if (n == 0) return WTHETA_OK;
     const int threads = 256;
     const int grid = (int)std::min<long long>((n + threads - 1) / threads, 1 << 20);
-    k_radec_to_xyz<<<grid, threads, 0, (cudaStream_t)stream>>>(rd, n, n, xyz, n, nullptr, 1.f);
+    k_radec_to_xyz<<<grid, threads, 0, (cudaStream_t)stream>>>(rd, n, xyz, n);
     count_launch();
     return check_cuda(cudaGetLastError());
 }

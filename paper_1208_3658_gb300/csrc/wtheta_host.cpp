@@ -167,8 +167,10 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
             e[0] = bands[which].lo; e[1] = bands[which].hi;
             e[2] = (uint32_t)bands[which].k; e[3] = (uint32_t)(bands[which].k + 1);
         } else {
-            e[0] = 0u; e[1] = 0xFFFFFFFFu;  // every value of the bucket is rechecked
-            e[2] = 0u; e[3] = 0u;
+            // every in-range value of the bucket is rechecked in FP64; one
+            // beyond the top edge (only the top bucket can hold one) is overflow
+            e[0] = 0u; e[1] = 0xFFFFFFFFu;
+            e[2] = (uint32_t)(K + 1); e[3] = (uint32_t)(K + 1);
             ++t->n_complex;
         }
     }

@@ -18,7 +18,9 @@ constexpr int kMaxLut = 512;       // entries of the FP32 screening table
 //   - else idx = max((bits >> shift) - base, 0), e = lut[idx] and
 //       bits < e.x -> slot e.z,  bits > e.y -> slot e.w,
 //       otherwise the pair is inside an edge's guard band (or the bucket holds
-//       more than one band) and is recomputed in FP64 against c64.
+//       more than one band) and is recomputed in FP64 against c64;
+//   - slot K+1 (overflow) in the table, and any value beyond h_top, goes to a
+//     trash row that is never added to the counts.
 struct BinTable {
     int32_t K;
     uint32_t h_top;        // FP32 bits of the top edge's upper guard bound

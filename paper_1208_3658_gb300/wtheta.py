@@ -25,7 +25,7 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 NOALLOC_MAX_POINTS, NOALLOC_TILE = 262144, 1024
 BINS_LINEAR, BINS_LN, BINS_LOG10 = 0, 1, 2
 DERR_NONFINITE, DERR_DEC_RANGE, DERR_NOT_UNIT = 1, 2, 4
-STAT_PAIRS, STAT_BINNED, STAT_RECHECK, STAT_TILES, NSTATS = 0, 1, 2, 3, 4
+STAT_PAIRS, STAT_RECHECK, STAT_TILES, STAT_SKIPPED, NSTATS = 0, 1, 2, 3, 4
 
 _lock = threading.Lock()
 _lib = None
@@ -39,7 +39,8 @@ class WthetaError(RuntimeError):
 
 class wtheta_tune(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
-                ("hist_mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("hist_mode", ctypes.c_int32), ("j_per_screen", ctypes.c_int32),
+                ("deferred", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
 def declared_functions() -> list:
@@ -205,7 +206,8 @@ def wtheta_count_ex(coords_a, coords_b, coords_are_xyz: bool, edges_deg, is_auto
     t = None
     if tune:
         t = wtheta_tune(int(tune.get("threads", 0)), int(tune.get("points_per_thread", 0)),
-                        int(tune.get("hist_mode", 0)), 0)
+                        int(tune.get("hist_mode", 0)), int(tune.get("j_per_screen", 0)),
+                        int(tune.get("deferred", 0)), int(tune.get("blocks_per_sm", 0)))
     _check(lib().wtheta_count_ex(_dev_ptr(coords_a), na, _dev_ptr(coords_b), nb,
                                  1 if coords_are_xyz else 0, ep, len(e) - 1, 1 if is_auto else 0,
                                  _dev_ptr(counts), ctypes.byref(t) if t is not None else None,

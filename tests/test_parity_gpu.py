@@ -19,8 +19,13 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 ARCMIN = 1.0 / 60.0
-VARIANTS = [dict(threads=t, points_per_thread=r, hist_mode=h)
-            for t in (128, 256) for r in (4, 8) for h in (1, 2)]
+# every instantiated kernel shape: (threads, points per thread, B points per
+# screening test, histogram mode, deferred binning)
+SHAPES = [(128, 8, 2, 3, 2), (128, 8, 2, 3, 1), (128, 8, 2, 1, 2), (128, 8, 2, 2, 1),
+          (128, 8, 1, 3, 2), (64, 16, 2, 3, 2), (64, 16, 2, 2, 1), (128, 16, 2, 3, 2),
+          (256, 8, 2, 3, 2), (256, 8, 2, 2, 1)]
+VARIANTS = [dict(threads=a, points_per_thread=b, j_per_screen=c, hist_mode=d, deferred=f)
+            for a, b, c, d, f in SHAPES]
 
 
 @pytest.fixture(scope="module")
@@ -75,8 +80,8 @@ def test_radec_conversion_within_ulps(W):
     assert np.max(np.abs(got - want) / ulp) <= 4.0
 
 
-@pytest.mark.parametrize("tune", VARIANTS, ids=lambda t: "nt%d_r%d_h%d" % (
-    t["threads"], t["points_per_thread"], t["hist_mode"]))
+@pytest.mark.parametrize("tune", VARIANTS, ids=lambda t: "nt%d_r%d_j%d_h%d_d%d" % (
+    t["threads"], t["points_per_thread"], t["j_per_screen"], t["hist_mode"], t["deferred"]))
 def test_small_workload_bit_exact_p1(W, tune):
     """10k clustered + 10k random in a 10 deg patch, 16 log bins 1'-5 deg."""
     wl = synth.small()
@@ -121,7 +126,7 @@ def test_ragged_sizes_bit_exact(W, n):
     e = W.wtheta_edges(0.5 * ARCMIN, 2.0, 20)
     A = O.radec_to_xyz(a) if n else np.zeros((3, 0))
     B = O.radec_to_xyz(b)
-    for tune in (VARIANTS[0], VARIANTS[3], VARIANTS[6]):
+    for tune in (VARIANTS[0], VARIANTS[1], VARIANTS[3], VARIANTS[5], VARIANTS[6], VARIANTS[8]):
         got = gpu_count_xyz(W, A, None, e, True, tune=tune)
         want = O.count_xyz(A, None, e, True)
         assert np.array_equal(got, want), ("auto", n, got, want)
