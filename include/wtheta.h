@@ -164,6 +164,64 @@ int wtheta_count_ex(const double* coords_a, int64_t n_a, const double* coords_b,
                     const wtheta_tune* tune, uint64_t* stats, void* stream);
 
 /*
+ * Batched counts: the DD, DR and RR of many (data, randoms) catalogue pairs
+ * sharing one edge set, in one persistent launch captured in a CUDA graph.
+ * The paper's §4 motivates it: Monte-Carlo error estimates of w(theta) need
+ * many mock catalogues counted exactly.  Every count of every pair becomes a
+ * contiguous range of items (tile pairs) of one work queue, biggest count
+ * first; the CTAs of one launch take items from a device cursor, so the
+ * uneven catalogue sizes share the GPU without idle SMs.
+ *
+ *   cats: host array of n_cats entries; the pointers in them are device,
+ *     interleaved FP64 RA/Dec degrees, borrowed for the plan's lifetime (each
+ *     run reads their current contents).
+ *   tune: NULL = autotune at plan time (kernel shape and histogram mode timed
+ *     on a sample of this batch's work; results are cached per device for
+ *     batches of similar size and bin count); else the given shape.
+ *   stream: used for the plan-time preparation and autotuning.
+ *   *plan: receives the plan; free it with wtheta_batch_free.
+ * The plan owns its scratch (FP32/FP64 copies of every catalogue), its work
+ * table and its graph.
+ */
+typedef struct wtheta_catalog_pair {
+    const double* data;
+    int64_t n_data;
+    const double* rand;
+    int64_t n_rand;
+} wtheta_catalog_pair;
+
+typedef struct wtheta_plan wtheta_plan;
+
+int wtheta_batch_plan(const wtheta_catalog_pair* cats, int32_t n_cats,
+                      const double* bin_edges_deg, int32_t n_bins, const wtheta_tune* tune,
+                      void* stream, wtheta_plan** plan);
+
+/*
+ * Runs a plan: one graph replay (conversion and spatial ordering of every
+ * catalogue, the single pair-count launch, the overflow slots), then copies
+ * the counts to counts: device, n_cats x 3 x (K+2) uint64, laid out
+ * [cat][DD, DR, RR][slot].  Asynchronous on stream.
+ */
+int wtheta_batch_run(wtheta_plan* plan, uint64_t* counts, void* stream);
+
+/* What a plan chose and holds (host struct filled by wtheta_batch_info). */
+typedef struct wtheta_batch_info_t {
+    wtheta_tune tune;          /* the kernel shape in use                    */
+    int64_t n_items;           /* tile pairs in the work queue               */
+    int64_t pairs;             /* algorithmic pairs of all counts            */
+    int64_t evaluated_pairs;   /* pairs evaluated, tile padding included     */
+    int32_t n_counts;          /* 3 n_cats                                   */
+    int32_t graph_kernels;     /* kernel launches per replay                 */
+    float autotune_ms;         /* plan-time autotuning cost                  */
+    int32_t autotuned;         /* 1 if the shape came from the autotuner     */
+} wtheta_batch_info_t;
+
+int wtheta_batch_info(const wtheta_plan* plan, wtheta_batch_info_t* info);
+
+/* Releases a plan (synchronises its device work first). */
+int wtheta_batch_free(wtheta_plan* plan);
+
+/*
  * Allocation-free variant of wtheta_count_xyz (the paper has no counterpart).
  *
  * Some callers cannot let a library allocate device memory: a process whose

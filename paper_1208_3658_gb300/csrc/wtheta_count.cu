@@ -287,19 +287,30 @@ __global__ void k_finalize(unsigned long long* counts, int K, unsigned long long
 // ---------------------------------------------------------------------------
 // the pair-count kernel
 // ---------------------------------------------------------------------------
-struct PairParams {
+// One count: catalogue a against catalogue b (auto: a = b, pairs i < j).
+struct Segment {
     const float4* a32;       // FP32 points (x, y, z, original index bits), tile-padded
     const float4* b32;
     const double* a64;       // FP64 SoA in the original order, stride a64_stride
     const double* b64;
     long long a64_stride, b64_stride;
     long long tiles_a, tiles_b;
-    long long item_begin;    // first tile pair of this launch
-    long long n_items;       // tile pairs of this launch
+    long long item_begin;    // first global item (tile pair) of this count
+    long long n_items;       // tile pairs of this count
+    unsigned long long* counts;  // K+2 slots (slot K+1 filled by the finalize kernel)
+    unsigned long long total;    // pairs of the count: n(n-1)/2 or n_a n_b
     int is_auto;
+    int pad_;
+};
+
+struct PairParams {
+    Segment seg0;            // the count, when n_segs == 0
+    const Segment* segs;     // device table sorted by item_begin, when n_segs > 0
+    int n_segs;
     int items_per_flush;     // flush the uint32 histograms after this many items
+    long long item_begin;    // this launch takes global items [item_begin, item_begin + n_items)
+    long long n_items;
     unsigned long long* cursor;
-    unsigned long long* counts;   // K+2 slots (slot K+1 filled by k_finalize)
     unsigned long long* stats;    // WTHETA_NSTATS or null
     BinTable tab;
 };
@@ -334,13 +345,13 @@ __device__ __forceinline__ void item_to_tiles(long long t, long long T_a, long l
 // FP64 recheck: the definition's squared chord and slot for the pair of
 // sorted positions (ia, jb), found in the caller's FP64 arrays through the
 // original indices kept in the FP32 copies.
-__device__ __forceinline__ unsigned recheck_slot(const PairParams& p, long long ia, long long jb,
+__device__ __forceinline__ unsigned recheck_slot(const Segment& S, long long ia, long long jb,
                                                  const double* __restrict__ c64, int K) {
-    const long long i = __float_as_int(p.a32[ia].w);
-    const long long j = __float_as_int(p.b32[jb].w);
-    const double* a = p.a64;
-    const double* b = p.b64;
-    const long long as = p.a64_stride, bs = p.b64_stride;
+    const long long i = __float_as_int(S.a32[ia].w);
+    const long long j = __float_as_int(S.b32[jb].w);
+    const double* a = S.a64;
+    const double* b = S.b64;
+    const long long as = S.a64_stride, bs = S.b64_stride;
     const double dx = __dsub_rn(a[i], b[j]);
     const double dy = __dsub_rn(a[as + i], b[bs + j]);
     const double dz = __dsub_rn(a[2 * as + i], b[2 * bs + j]);
@@ -408,7 +419,7 @@ __device__ __forceinline__ void hist_inc(unsigned cell) {
 template <int NT, int R, int NV, int HM>
 __device__ __forceinline__ void bin_values(const float (&s)[NV], unsigned col, unsigned lut,
                                            int shift, int base, int top_idx, unsigned h_top,
-                                           unsigned row_bytes, int K, const PairParams& p,
+                                           unsigned row_bytes, int K, const Segment& S,
                                            long long a0, long long bj,
                                            const double* __restrict__ sC,
                                            unsigned long long& n_recheck) {
@@ -426,7 +437,7 @@ __device__ __forceinline__ void bin_values(const float (&s)[NV], unsigned col, u
     while (amb_mask) {
         const int v = __ffs(amb_mask) - 1;
         amb_mask &= amb_mask - 1;
-        const unsigned slot = recheck_slot(p, a0 + (v % R) * NT, bj + v / R, sC, K);
+        const unsigned slot = recheck_slot(S, a0 + (v % R) * NT, bj + v / R, sC, K);
         ++n_recheck;
         hist_inc<HM>(col + slot * row_bytes);
     }
@@ -477,7 +488,8 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
                                           const double* __restrict__ sC, unsigned hist,
                                           const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
                                           const f2_t (&az)[R / 2], const PairParams& p,
-                                          long long I, long long J, unsigned long long& n_recheck) {
+                                          const Segment& S, long long I, long long J,
+                                          unsigned long long& n_recheck) {
     using PK = PairKernel<NT, R, JU, HM, DEF>;
     constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
     constexpr int NV = JU * R;
@@ -510,7 +522,7 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
                 float s[NV];
                 chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
                 bin_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx, h_top, row_bytes, K,
-                                          p, a0, b0 + j, sC, n_recheck);
+                                          S, a0, b0 + j, sC, n_recheck);
             }
         }
         return;
@@ -523,7 +535,7 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
 
         if (HM != kHistWarp) {
             if (!(m <= hf)) continue;
-            bin_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx, h_top, row_bytes, K, p,
+            bin_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx, h_top, row_bytes, K, S,
                                       a0, b0 + j, sC, n_recheck);
         } else {
             if (!__any_sync(0xffffffffu, m <= hf)) continue;
@@ -541,7 +553,7 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
             while (amb_mask) {
                 const int v = __ffs(amb_mask) - 1;
                 amb_mask &= amb_mask - 1;
-                const unsigned slot = recheck_slot(p, a0 + (v % R) * NT, b0 + j + v / R, sC, K);
+                const unsigned slot = recheck_slot(S, a0 + (v % R) * NT, b0 + j + v / R, sC, K);
                 ++n_recheck;
                 red_add_shared(col + slot * row_bytes, 1u);
             }
@@ -571,16 +583,46 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
     for (int q = tid; q <= K; q += NT) sC[q] = p.tab.c64[q];
     for (int q = tid; q < (K + 2) * HCOLS; q += NT) hist[q] = 0u;
 
+    // the current count lives in shared memory; thread 0 switches it when an
+    // item of another count is claimed, after the block flushed its columns
+    __shared__ Segment sSeg;
+    __shared__ int s_seg;
     unsigned long long n_recheck = 0, n_items = 0;
-    int since_flush = 0;
+    int since_flush = 0, cur_seg = -2;
     for (;;) {
-        if (tid == 0) s_item = (long long)atomicAdd(p.cursor, 1ull);
+        if (tid == 0) {
+            const long long t = (long long)atomicAdd(p.cursor, 1ull);
+            s_item = t;
+            int seg = -1;
+            if (t < p.n_items && p.n_segs > 0) {
+                const long long g = p.item_begin + t;
+                int lo = 0, hi = p.n_segs - 1;  // last segment with item_begin <= g
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (p.segs[mid].item_begin <= g) lo = mid; else hi = mid - 1;
+                }
+                seg = lo;
+            }
+            s_seg = seg;
+        }
         __syncthreads();  // s_item visible; previous item's shared reads finished
         const long long t = s_item;
         if (t >= p.n_items) break;
+        const int seg = s_seg;
+        if (seg != cur_seg) {
+            if (cur_seg != -2 && since_flush > 0) {
+                flush_hist<NT, HCOLS>(hist, K, sSeg.counts);
+                since_flush = 0;
+            }
+            __syncthreads();  // flush done before the segment is replaced
+            if (tid == 0) sSeg = seg < 0 ? p.seg0 : p.segs[seg];
+            cur_seg = seg;
+            __syncthreads();
+        }
+        const Segment& S = sSeg;
         long long I, J;
-        item_to_tiles(p.item_begin + t, p.tiles_a, p.tiles_b, p.is_auto, &I, &J);
-        const float4* gB = p.b32 + J * TB;
+        item_to_tiles(p.item_begin + t - S.item_begin, S.tiles_a, S.tiles_b, S.is_auto, &I, &J);
+        const float4* gB = S.b32 + J * TB;
 #pragma unroll 4
         for (int q = 0; q < R; ++q) {
             const float4 b = gB[q * NT + tid];
@@ -594,7 +636,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
         // place from the vector-load destinations, a layout measured to cost
         // about a quarter of the screening loop's throughput.
         f2_t ax[R / 2], ay[R / 2], az[R / 2];
-        const float4* gA = p.a32 + I * TA;
+        const float4* gA = S.a32 + I * TA;
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) {
             const float4 u = gA[(2 * q) * NT + tid];
@@ -606,22 +648,22 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
         __syncthreads();  // B tile staged
         const unsigned a_bxy = smem_addr(sBxy), a_bz = smem_addr(sBz), a_lut = smem_addr(sLut),
                        a_hist = smem_addr(hist);
-        if (p.is_auto && I == J)
-            tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, sC, a_hist, ax, ay, az, p, I,
+        if (S.is_auto && I == J)
+            tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, sC, a_hist, ax, ay, az, p, S, I,
                                                 J, n_recheck);
         else
-            tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, sC, a_hist, ax, ay, az, p, I,
-                                                 J, n_recheck);
+            tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, sC, a_hist, ax, ay, az, p, S,
+                                                 I, J, n_recheck);
         ++n_items;
         if (++since_flush == p.items_per_flush) {
             __syncthreads();
-            flush_hist<NT, HCOLS>(hist, K, p.counts);
+            flush_hist<NT, HCOLS>(hist, K, sSeg.counts);
             __syncthreads();
             since_flush = 0;
         }
     }
     // all threads left the loop after the same barrier
-    flush_hist<NT, HCOLS>(hist, K, p.counts);
+    if (cur_seg != -2) flush_hist<NT, HCOLS>(hist, K, sSeg.counts);
     if (p.stats) {
         unsigned long long v = n_recheck;
 #pragma unroll
@@ -631,6 +673,16 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
             atomicAdd(p.stats + WTHETA_STAT_TILES, n_items);
             atomicAdd(p.stats + WTHETA_STAT_PAIRS, n_items * (unsigned long long)TA * TB);
         }
+    }
+}
+
+// counts[K+1] = total - sum(counts[0..K]) for every count of a batch.
+__global__ void k_finalize_segments(const Segment* __restrict__ segs, int n_segs, int K) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_segs; i += gridDim.x * blockDim.x) {
+        unsigned long long* c = segs[i].counts;
+        unsigned long long s = 0;
+        for (int k = 0; k <= K; ++k) s += c[k];
+        c[K + 1] = segs[i].total - s;
     }
 }
 
@@ -813,25 +865,44 @@ static int prepare(const double* coords, long long n, long long n_pad, int is_xy
     return check_cuda(cudaGetLastError());
 }
 
-static PairParams make_params(const Variant* v, const BinTable& tab, const Prepared& A,
-                              const Prepared& B, long long ta, long long tb, int is_auto,
-                              long long item_begin, long long n_items,
-                              unsigned long long* cursor, unsigned long long* counts,
+static unsigned long long per_item_bound(const Variant* v) {
+    // a thread evaluates R x TB pairs per item, so a histogram cell gains at
+    // most R TB (private per-thread column) or 32 R TB (per-warp column)
+    return (v->hm == kHistWarp ? 32ull : 1ull) * (unsigned long long)v->r *
+           (unsigned long long)v->nt * (unsigned long long)v->r;
+}
+
+static Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
+                            int is_auto, long long item_begin, unsigned long long* counts,
+                            unsigned long long total) {
+    Segment g;
+    std::memset(&g, 0, sizeof(g));
+    g.a32 = A.p32; g.b32 = B.p32; g.a64 = A.x64; g.b64 = B.x64;
+    g.a64_stride = A.stride; g.b64_stride = B.stride;
+    g.tiles_a = ta; g.tiles_b = tb;
+    g.item_begin = item_begin;
+    g.n_items = is_auto ? ta * (ta + 1) / 2 : ta * tb;
+    g.counts = counts;
+    g.total = total;
+    g.is_auto = is_auto;
+    return g;
+}
+
+static PairParams make_params(const Variant* v, const BinTable& tab, const Segment* seg0,
+                              const Segment* segs, int n_segs, long long item_begin,
+                              long long n_items, unsigned long long* cursor,
                               unsigned long long* stats) {
     PairParams prm;
     std::memset(&prm, 0, sizeof(prm));
-    prm.a32 = A.p32; prm.b32 = B.p32; prm.a64 = A.x64; prm.b64 = B.x64;
-    prm.a64_stride = A.stride; prm.b64_stride = B.stride;
-    prm.tiles_a = ta; prm.tiles_b = tb;
-    prm.item_begin = item_begin; prm.n_items = n_items;
-    prm.is_auto = is_auto;
-    // a thread evaluates R x TB pairs per item, so a histogram cell gains at
-    // most R TB (private per-thread column) or 32 R TB (per-warp column)
-    const unsigned long long per_item = (v->hm == kHistWarp ? 32ull : 1ull) *
-                                        (unsigned long long)v->r * (unsigned long long)v->nt *
-                                        (unsigned long long)v->r;
-    prm.items_per_flush = (int)std::min<unsigned long long>(0xFFFFFFFFull / per_item, 1ull << 30);
-    prm.cursor = cursor; prm.counts = counts; prm.stats = stats;
+    if (seg0) prm.seg0 = *seg0;
+    prm.segs = segs;
+    prm.n_segs = n_segs;
+    prm.item_begin = item_begin;
+    prm.n_items = n_items;
+    prm.items_per_flush = (int)std::min<unsigned long long>(0xFFFFFFFFull / per_item_bound(v),
+                                                            1ull << 30);
+    prm.cursor = cursor;
+    prm.stats = stats;
     std::memcpy(&prm.tab, &tab, sizeof(tab));
     return prm;
 }
@@ -900,8 +971,8 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
     if (!rc) rc = grid_for(v, smem, n_items, di.sm_count, want_per_sm, &grid);
     if (!rc) {
-        const PairParams prm = make_params(v, tab, A, B, ta, tb, is_auto, 0, n_items, cursor,
-                                           counts, stats);
+        const Segment seg = make_segment(A, B, ta, tb, is_auto, 0, counts, total);
+        const PairParams prm = make_params(v, tab, &seg, nullptr, 0, 0, n_items, cursor, stats);
         v->kernel<<<grid, v->nt, smem, st>>>(prm);
         count_launch();
         rc = check_cuda(cudaGetLastError());
@@ -1005,23 +1076,333 @@ static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double*
     const size_t smem = v->smem(K, tab.n_lut);
     int grid = 0;
     if ((rc = grid_for(v, smem, n_items, di.sm_count, 0, &grid))) return rc;
-    PairParams prm;
-    std::memset(&prm, 0, sizeof(prm));
-    prm.a32 = a32; prm.b32 = b32; prm.a64 = ca; prm.b64 = cb;
-    prm.a64_stride = n_a; prm.b64_stride = n_b;
-    prm.tiles_a = ta; prm.tiles_b = tb; prm.n_items = n_items;
-    prm.is_auto = is_auto;
-    const unsigned long long per_item = (v->hm == kHistWarp ? 32ull : 1ull) *
-                                        (unsigned long long)v->r * (unsigned long long)T;
-    prm.items_per_flush = (int)std::min<unsigned long long>(0xFFFFFFFFull / per_item, 1ull << 30);
-    prm.cursor = cursor; prm.counts = counts; prm.stats = nullptr;
-    std::memcpy(&prm.tab, &tab, sizeof(tab));
+    Prepared A, B;
+    A.p32 = a32; A.x64 = ca; A.stride = n_a;
+    B.p32 = b32; B.x64 = cb; B.stride = n_b;
+    const Segment seg = make_segment(A, B, ta, tb, is_auto, 0, counts, total);
+    const PairParams prm = make_params(v, tab, &seg, nullptr, 0, 0, n_items, cursor, nullptr);
     v->kernel<<<grid, v->nt, smem, st>>>(prm);
     count_launch();
     if ((rc = check_cuda(cudaGetLastError()))) return rc;
     k_finalize<<<1, 1, 0, st>>>(counts, K, total);
     count_launch();
     return check_cuda(cudaGetLastError());
+}
+
+}  // namespace wtheta
+
+// ---------------------------------------------------------------------------
+// batched counts: one work queue over many catalogue pairs, one graph
+// ---------------------------------------------------------------------------
+
+struct wtheta_plan {
+    int dev = 0;
+    int K = 0;
+    int n_cats = 0;
+    wtheta::BinTable tab;
+    const wtheta::Variant* v = nullptr;
+    wtheta_tune tune = {};
+    int autotuned = 0;
+    float autotune_ms = 0.f;
+    std::vector<wtheta_catalog_pair> cats;
+    void* scratch = nullptr;               // prepared copies of every catalogue
+    std::vector<wtheta::Prepared> prep;    // 2 per catalogue pair
+    std::vector<long long> n_pad;
+    wtheta::Segment* d_segs = nullptr;
+    int n_segs = 0;
+    long long total_items = 0;
+    long long pairs = 0;
+    unsigned long long* d_counts = nullptr;  // internal: [cat][kind][K+2]
+    unsigned long long* d_cursor = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_kernels = 0;
+    int grid = 0;
+    size_t smem = 0;
+};
+
+namespace wtheta {
+
+// Autotuner cache: the shape picked for batches of similar work on a device
+// of this size, keyed by (SM count, K, log2 of the batch's pair count).
+struct TuneKey {
+    int sm, K, size_bucket;
+};
+static std::mutex g_tune_mu;
+static std::vector<std::pair<TuneKey, int>> g_tune_cache;
+
+static int lookup_tuned(const TuneKey& k) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    for (auto& e : g_tune_cache)
+        if (e.first.sm == k.sm && e.first.K == k.K && e.first.size_bucket == k.size_bucket)
+            return e.second;
+    return -1;
+}
+
+static void store_tuned(const TuneKey& k, int idx) {
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune_cache.push_back({k, idx});
+}
+
+// Lays out the plan's scratch and work table for one kernel shape (its tile
+// T = threads x points_per_thread), prepares every catalogue on stream st.
+static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStream_t st) {
+    const long long T = (long long)v->nt * v->r;
+    const int nc = P->n_cats;
+    // scratch: the cursor head, then each catalogue's prepared copies
+    std::vector<size_t> off(2 * nc);
+    size_t bytes = 256;
+    P->n_pad.assign(2 * nc, 0);
+    for (int m = 0; m < nc; ++m) {
+        const long long nd = P->cats[m].n_data, nr = P->cats[m].n_rand;
+        P->n_pad[2 * m] = round_up(nd, T);
+        P->n_pad[2 * m + 1] = round_up(nr, T);
+        off[2 * m] = bytes;
+        bytes += (prepare_bytes(nd, P->n_pad[2 * m], 0) + 255) / 256 * 256;
+        off[2 * m + 1] = bytes;
+        bytes += (prepare_bytes(nr, P->n_pad[2 * m + 1], 0) + 255) / 256 * 256;
+    }
+    if (P->scratch) cudaFree(P->scratch);
+    P->scratch = nullptr;
+    int rc = check_cuda(cudaMalloc(&P->scratch, bytes));
+    if (rc) return rc;
+    unsigned char* base = (unsigned char*)P->scratch;
+    P->d_cursor = (unsigned long long*)base;
+    P->prep.assign(2 * nc, Prepared());
+    for (int m = 0; m < nc; ++m) {
+        rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], 0, 1.f, base + off[2 * m],
+                     sm_count, st, &P->prep[2 * m]);
+        if (!rc)
+            rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, -1.f,
+                         base + off[2 * m + 1], sm_count, st, &P->prep[2 * m + 1]);
+        if (rc) return rc;
+    }
+    // the work table: DD, DR, RR of every pair, biggest count first
+    std::vector<Segment> segs;
+    P->pairs = 0;
+    for (int m = 0; m < nc; ++m) {
+        const long long nd = P->cats[m].n_data, nr = P->cats[m].n_rand;
+        const long long td = P->n_pad[2 * m] / T, tr = P->n_pad[2 * m + 1] / T;
+        unsigned long long* c = P->d_counts + (size_t)3 * m * (P->K + 2);
+        const unsigned long long ndd = (unsigned long long)nd * (unsigned long long)(nd - 1) / 2;
+        const unsigned long long ndr = (unsigned long long)nd * (unsigned long long)nr;
+        const unsigned long long nrr = (unsigned long long)nr * (unsigned long long)(nr - 1) / 2;
+        P->pairs += (long long)(ndd + ndr + nrr);
+        segs.push_back(make_segment(P->prep[2 * m], P->prep[2 * m], td, td, 1, 0, c, ndd));
+        segs.push_back(make_segment(P->prep[2 * m], P->prep[2 * m + 1], td, tr, 0, 0,
+                                    c + (P->K + 2), ndr));
+        segs.push_back(make_segment(P->prep[2 * m + 1], P->prep[2 * m + 1], tr, tr, 1, 0,
+                                    c + 2 * (P->K + 2), nrr));
+    }
+    std::stable_sort(segs.begin(), segs.end(),
+                     [](const Segment& a, const Segment& b) { return a.n_items > b.n_items; });
+    long long items = 0;
+    for (auto& g : segs) {
+        g.item_begin = items;
+        items += g.n_items;
+    }
+    P->total_items = items;
+    P->n_segs = (int)segs.size();
+    if (P->d_segs) cudaFree(P->d_segs);
+    P->d_segs = nullptr;
+    if ((rc = check_cuda(cudaMalloc(&P->d_segs, sizeof(Segment) * segs.size())))) return rc;
+    return check_cuda(cudaMemcpyAsync(P->d_segs, segs.data(), sizeof(Segment) * segs.size(),
+                                      cudaMemcpyHostToDevice, st));
+}
+
+static int launch_batch_pairs(wtheta_plan* P, const Variant* v, long long item_begin,
+                              long long n_items, int grid, size_t smem, cudaStream_t st) {
+    const PairParams prm = make_params(v, P->tab, nullptr, P->d_segs, P->n_segs, item_begin,
+                                       n_items, P->d_cursor, nullptr);
+    v->kernel<<<grid, v->nt, smem, st>>>(prm);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
+// Times each candidate shape on the first items of the queue (the biggest
+// counts) and keeps the fastest per item.  Candidates share a tile size per
+// layout; a different tile size re-lays the plan out.
+static int autotune(wtheta_plan* P, const DeviceInfo& di, cudaStream_t st, int* best_idx) {
+    int nv = 0;
+    const Variant* vs = variants(&nv);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return WTHETA_ECUDA;
+    float best = 1e30f;
+    int rc = WTHETA_OK;
+    long long cur_T = -1;
+    for (int i = 0; i < nv && !rc; ++i) {
+        const Variant* v = &vs[i];
+        const size_t smem = v->smem(P->K, P->tab.n_lut);
+        if (smem > (size_t)di.max_smem_optin) continue;
+        const long long T = (long long)v->nt * v->r;
+        if (T != cur_T) {
+            if ((rc = plan_layout(P, v, di.sm_count, st))) break;
+            cur_T = T;
+        }
+        int grid = 0;
+        if ((rc = grid_for(v, smem, P->total_items, di.sm_count, 0, &grid))) break;
+        // a sample of several items per CTA, from the front of the queue
+        const long long n_sample =
+            std::min<long long>(P->total_items, std::max<long long>(8LL * grid, P->total_items / 64));
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && !rc; ++rep) {  // first pass warms up
+            rc = check_cuda(cudaMemsetAsync(P->d_cursor, 0, 8, st));
+            if (!rc) rc = check_cuda(cudaEventRecord(e0, st));
+            if (!rc) rc = launch_batch_pairs(P, v, 0, n_sample, grid, smem, st);
+            if (!rc) rc = check_cuda(cudaEventRecord(e1, st));
+            if (!rc) rc = check_cuda(cudaEventSynchronize(e1));
+            if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        if (rc) break;
+        const float per = ms / (float)n_sample;
+        if (per < best) {
+            best = per;
+            *best_idx = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+static int plan_capture(wtheta_plan* P, const DeviceInfo& di) {
+    cudaStream_t cs;
+    int rc = check_cuda(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    if (rc) return rc;
+    const unsigned long long launches0 = g_launches.load();
+    rc = check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    if (!rc) {
+        // re-prepare every catalogue from its current RA/Dec, then count
+        unsigned char* base = (unsigned char*)P->scratch;
+        for (int m = 0; m < P->n_cats && !rc; ++m) {
+            Prepared a, b;
+            const size_t off_a = (size_t)((const unsigned char*)P->prep[2 * m].p32 - base);
+            const size_t off_b = (size_t)((const unsigned char*)P->prep[2 * m + 1].p32 - base);
+            rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], 0, 1.f, base + off_a,
+                         di.sm_count, cs, &a);
+            if (!rc)
+                rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, -1.f,
+                             base + off_b, di.sm_count, cs, &b);
+        }
+        const size_t nbytes = (size_t)P->n_cats * 3 * (P->K + 2) * sizeof(unsigned long long);
+        if (!rc) rc = check_cuda(cudaMemsetAsync(P->d_counts, 0, nbytes, cs));
+        if (!rc) rc = check_cuda(cudaMemsetAsync(P->d_cursor, 0, 8, cs));
+        if (!rc) rc = launch_batch_pairs(P, P->v, 0, P->total_items, P->grid, P->smem, cs);
+        if (!rc) {
+            k_finalize_segments<<<(P->n_segs + 127) / 128, 128, 0, cs>>>(P->d_segs, P->n_segs,
+                                                                        P->K);
+            count_launch();
+            rc = check_cuda(cudaGetLastError());
+        }
+        cudaGraph_t g = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+        if (!rc) rc = check_cuda(ce);
+        if (!rc) {
+            P->graph = g;
+            rc = check_cuda(cudaGraphInstantiate(&P->exec, g, 0));
+        } else if (g) {
+            cudaGraphDestroy(g);
+        }
+    }
+    // launches recorded during capture are replayed, not launched: uncount them
+    P->graph_kernels = (int)(g_launches.load() - launches0);
+    g_launches.fetch_sub(P->graph_kernels);
+    cudaStreamDestroy(cs);
+    return rc;
+}
+
+static void plan_release(wtheta_plan* P) {
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    if (P->scratch) cudaFree(P->scratch);
+    if (P->d_segs) cudaFree(P->d_segs);
+    if (P->d_counts) cudaFree(P->d_counts);
+    delete P;
+}
+
+static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, const double* edges, int K,
+                           const wtheta_tune* tune, cudaStream_t st, wtheta_plan** out) {
+    if (!out || !cats || n_cats < 1) return WTHETA_EINVAL;
+    for (int m = 0; m < n_cats; ++m) {
+        const wtheta_catalog_pair& c = cats[m];
+        if (c.n_data < 2 || c.n_rand < 2 || !c.data || !c.rand) return WTHETA_EINVAL;
+    }
+    if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
+                 tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
+                 tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0))
+        return WTHETA_EINVAL;
+    wtheta_plan* P = new wtheta_plan();
+    P->K = K;
+    P->n_cats = n_cats;
+    P->cats.assign(cats, cats + n_cats);
+    int rc = build_table(edges, K, &P->tab);
+    DeviceInfo di;
+    if (!rc) rc = device_info(&di);
+    if (!rc) rc = check_cuda(cudaGetDevice(&P->dev));
+    if (!rc)
+        rc = check_cuda(cudaMalloc(&P->d_counts, (size_t)n_cats * 3 * (K + 2) * sizeof(unsigned long long)));
+    if (rc) {
+        plan_release(P);
+        return rc;
+    }
+    int nv = 0;
+    const Variant* vs = variants(&nv);
+    if (tune) {
+        P->v = pick_variant(tune, K, P->tab.n_lut, di.max_smem_optin);
+        if (!P->v) rc = WTHETA_EINVAL;
+    } else {
+        // size bucket: log2 of the batch's pairs
+        long long pairs = 0;
+        for (int m = 0; m < n_cats; ++m)
+            pairs += cats[m].n_data * cats[m].n_data / 2 + cats[m].n_data * cats[m].n_rand +
+                     cats[m].n_rand * cats[m].n_rand / 2;
+        int bucket = 0;
+        while ((1LL << (bucket + 1)) <= pairs && bucket < 62) ++bucket;
+        const TuneKey key{di.sm_count, K, bucket};
+        int idx = lookup_tuned(key);
+        if (idx < 0) {
+            cudaEvent_t t0, t1;
+            cudaEventCreate(&t0);
+            cudaEventCreate(&t1);
+            cudaEventRecord(t0, st);
+            rc = autotune(P, di, st, &idx);
+            cudaEventRecord(t1, st);
+            cudaEventSynchronize(t1);
+            cudaEventElapsedTime(&P->autotune_ms, t0, t1);
+            cudaEventDestroy(t0);
+            cudaEventDestroy(t1);
+            if (!rc && idx >= 0) store_tuned(key, idx);
+        }
+        if (!rc && idx < 0) rc = WTHETA_EINVAL;
+        if (!rc) {
+            P->v = &vs[idx];
+            P->autotuned = 1;
+        }
+    }
+    if (!rc) {
+        P->tune.threads = P->v->nt;
+        P->tune.points_per_thread = P->v->r;
+        P->tune.j_per_screen = P->v->ju;
+        P->tune.hist_mode = P->v->hm;
+        P->tune.deferred = P->v->def + 1;
+        P->smem = P->v->smem(K, P->tab.n_lut);
+        rc = plan_layout(P, P->v, di.sm_count, st);
+    }
+    if (!rc) rc = grid_for(P->v, P->smem, P->total_items, di.sm_count,
+                           tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0, &P->grid);
+    if (!rc) {
+        P->tune.blocks_per_sm = (P->grid + di.sm_count - 1) / di.sm_count;
+        rc = check_cuda(cudaStreamSynchronize(st));
+    }
+    if (!rc) rc = plan_capture(P, di);
+    if (rc) {
+        cudaStreamSynchronize(st);
+        plan_release(P);
+        return rc;
+    }
+    *out = P;
+    return WTHETA_OK;
 }
 
 }  // namespace wtheta
@@ -1065,6 +1446,46 @@ int wtheta_count_xyz_noalloc(const double* a, int64_t n_a, const double* b, int6
                              void* stream) {
     return count_xyz_noalloc_impl(a, n_a, b, n_b, edges, K, is_auto, (unsigned long long*)counts,
                                   (cudaStream_t)stream);
+}
+
+int wtheta_batch_plan(const wtheta_catalog_pair* cats, int32_t n_cats, const double* edges,
+                      int32_t K, const wtheta_tune* tune, void* stream, wtheta_plan** plan) {
+    return batch_plan_impl(cats, n_cats, edges, K, tune, (cudaStream_t)stream, plan);
+}
+
+int wtheta_batch_run(wtheta_plan* P, uint64_t* counts, void* stream) {
+    if (!P || !counts) return WTHETA_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return WTHETA_ECUDA;
+    if (dev != P->dev) return WTHETA_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = check_cuda(cudaGraphLaunch(P->exec, st));
+    if (rc) return rc;
+    count_launch((unsigned)P->graph_kernels);
+    const size_t bytes = (size_t)P->n_cats * 3 * (P->K + 2) * sizeof(unsigned long long);
+    return check_cuda(cudaMemcpyAsync(counts, P->d_counts, bytes, cudaMemcpyDeviceToDevice, st));
+}
+
+int wtheta_batch_info(const wtheta_plan* P, wtheta_batch_info_t* info) {
+    if (!P || !info) return WTHETA_EINVAL;
+    std::memset(info, 0, sizeof(*info));
+    info->tune = P->tune;
+    info->n_items = P->total_items;
+    info->pairs = P->pairs;
+    const long long T = (long long)P->v->nt * P->v->r;
+    info->evaluated_pairs = P->total_items * T * T;
+    info->n_counts = 3 * P->n_cats;
+    info->graph_kernels = P->graph_kernels;
+    info->autotune_ms = P->autotune_ms;
+    info->autotuned = P->autotuned;
+    return WTHETA_OK;
+}
+
+int wtheta_batch_free(wtheta_plan* P) {
+    if (!P) return WTHETA_EINVAL;
+    cudaDeviceSynchronize();
+    plan_release(P);
+    return WTHETA_OK;
 }
 
 uint64_t wtheta_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

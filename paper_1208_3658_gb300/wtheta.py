@@ -43,6 +43,18 @@ class wtheta_tune(ctypes.Structure):
                 ("deferred", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
 
 
+class wtheta_catalog_pair(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("n_data", ctypes.c_int64),
+                ("rand", ctypes.c_void_p), ("n_rand", ctypes.c_int64)]
+
+
+class wtheta_batch_info_t(ctypes.Structure):
+    _fields_ = [("tune", wtheta_tune), ("n_items", ctypes.c_int64), ("pairs", ctypes.c_int64),
+                ("evaluated_pairs", ctypes.c_int64), ("n_counts", ctypes.c_int32),
+                ("graph_kernels", ctypes.c_int32), ("autotune_ms", ctypes.c_float),
+                ("autotuned", ctypes.c_int32)]
+
+
 def declared_functions() -> list:
     """Names of the functions include/wtheta.h declares."""
     text = open(HEADER).read()
@@ -77,6 +89,12 @@ def lib() -> ctypes.CDLL:
             L.wtheta_ls_cross.argtypes = [u64p, u64p, u64p, u64p, i64, i64, i64, i64, i32, dp]
             L.wtheta_correlate.argtypes = [dp, i64, dp, i64, dp, i32, u64p, dp, vp]
             L.wtheta_count_xyz_noalloc.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
+            L.wtheta_batch_plan.argtypes = [ctypes.POINTER(wtheta_catalog_pair), i32, dp, i32,
+                                            ctypes.POINTER(wtheta_tune), vp,
+                                            ctypes.POINTER(ctypes.c_void_p)]
+            L.wtheta_batch_run.argtypes = [vp, vp, vp]
+            L.wtheta_batch_info.argtypes = [vp, ctypes.POINTER(wtheta_batch_info_t)]
+            L.wtheta_batch_free.argtypes = [vp]
             L.wtheta_kernel_launches.argtypes = []
             L.wtheta_kernel_launches.restype = ctypes.c_uint64
             _lib = L
@@ -197,17 +215,79 @@ def wtheta_count_xyz_noalloc(xyz_a, xyz_b, edges_deg, is_auto: bool, counts, str
            "wtheta_count_xyz_noalloc")
 
 
+def _tune_struct(tune):
+    if not tune:
+        return None
+    return wtheta_tune(int(tune.get("threads", 0)), int(tune.get("points_per_thread", 0)),
+                       int(tune.get("hist_mode", 0)), int(tune.get("j_per_screen", 0)),
+                       int(tune.get("deferred", 0)), int(tune.get("blocks_per_sm", 0)))
+
+
+class BatchPlan:
+    """A wtheta_batch_plan handle; keeps the catalogue tensors it borrows alive."""
+
+    def __init__(self, handle, tensors, n_cats, n_bins):
+        self.handle = handle
+        self._tensors = tensors
+        self.n_cats = n_cats
+        self.n_bins = n_bins
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib().wtheta_batch_free(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def wtheta_batch_plan(cats, edges_deg, tune: dict | None = None, stream=None) -> BatchPlan:
+    """cats: list of (data, rand) CUDA float64 tensors of interleaved RA/Dec."""
+    e, ep = _host_f64(edges_deg)
+    arr = (wtheta_catalog_pair * len(cats))()
+    keep = []
+    for i, (d, r) in enumerate(cats):
+        arr[i] = wtheta_catalog_pair(_dev_ptr(d), _n_points(d, 2), _dev_ptr(r), _n_points(r, 2))
+        keep += [d, r]
+    t = _tune_struct(tune)
+    h = ctypes.c_void_p()
+    _check(lib().wtheta_batch_plan(arr, len(cats), ep, len(e) - 1,
+                                   ctypes.byref(t) if t is not None else None, _stream(stream),
+                                   ctypes.byref(h)), "wtheta_batch_plan")
+    return BatchPlan(h, keep, len(cats), len(e) - 1)
+
+
+def wtheta_batch_run(plan: BatchPlan, counts, stream=None):
+    """counts: CUDA 8-byte tensor of n_cats x 3 x (K+2) slots."""
+    _check(lib().wtheta_batch_run(plan.handle, _dev_ptr(counts), _stream(stream)),
+           "wtheta_batch_run")
+
+
+def wtheta_batch_info(plan: BatchPlan) -> dict:
+    info = wtheta_batch_info_t()
+    _check(lib().wtheta_batch_info(plan.handle, ctypes.byref(info)), "wtheta_batch_info")
+    t = info.tune
+    return dict(tune=dict(threads=t.threads, points_per_thread=t.points_per_thread,
+                          hist_mode=t.hist_mode, j_per_screen=t.j_per_screen,
+                          deferred=t.deferred, blocks_per_sm=t.blocks_per_sm),
+                n_items=info.n_items, pairs=info.pairs, evaluated_pairs=info.evaluated_pairs,
+                n_counts=info.n_counts, graph_kernels=info.graph_kernels,
+                autotune_ms=info.autotune_ms, autotuned=bool(info.autotuned))
+
+
+def wtheta_batch_free(plan: BatchPlan):
+    if plan.handle:
+        _check(lib().wtheta_batch_free(plan.handle), "wtheta_batch_free")
+        plan.handle = None
+
+
 def wtheta_count_ex(coords_a, coords_b, coords_are_xyz: bool, edges_deg, is_auto: bool, counts,
                     tune: dict | None = None, stats=None, stream=None):
     e, ep = _host_f64(edges_deg)
     per = 3 if coords_are_xyz else 2
     na = _n_points(coords_a, per)
     nb = na if is_auto else _n_points(coords_b, per)
-    t = None
-    if tune:
-        t = wtheta_tune(int(tune.get("threads", 0)), int(tune.get("points_per_thread", 0)),
-                        int(tune.get("hist_mode", 0)), int(tune.get("j_per_screen", 0)),
-                        int(tune.get("deferred", 0)), int(tune.get("blocks_per_sm", 0)))
+    t = _tune_struct(tune)
     _check(lib().wtheta_count_ex(_dev_ptr(coords_a), na, _dev_ptr(coords_b), nb,
                                  1 if coords_are_xyz else 0, ep, len(e) - 1, 1 if is_auto else 0,
                                  _dev_ptr(counts), ctypes.byref(t) if t is not None else None,

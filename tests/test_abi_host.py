@@ -182,3 +182,19 @@ def test_fp32_error_bound_random_pairs():
     err = np.abs(s32 - s64)[ok]
     assert ok.sum() > 100_000
     assert np.all(err <= g[jj] / 2), np.max(err / (g[jj] / 2))
+
+
+def test_batch_plan_validation_needs_no_gpu():
+    L = W.lib()
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    ep = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    cats = (W.wtheta_catalog_pair * 2)()
+    cats[0] = W.wtheta_catalog_pair(16, 100, 32, 200)
+    cats[1] = W.wtheta_catalog_pair(16, 1, 32, 200)      # fewer than 2 data points
+    assert L.wtheta_batch_plan(cats, 2, ep, 16, None, None, ctypes.byref(h)) == -1
+    assert L.wtheta_batch_plan(cats, 0, ep, 16, None, None, ctypes.byref(h)) == -1
+    cats[1] = W.wtheta_catalog_pair(None, 100, 32, 200)   # null data pointer
+    assert L.wtheta_batch_plan(cats, 2, ep, 16, None, None, ctypes.byref(h)) == -1
+    assert L.wtheta_batch_run(None, None, None) == -1
+    assert L.wtheta_batch_free(None) == -1
