@@ -393,53 +393,72 @@ __device__ __forceinline__ void flush_hist(unsigned* hist, int K,
     }
 }
 
-// Byte offset of the histogram row of an FP32 squared chord.  The table
-// gives the row below / above the guard band of the bucket's edge; values
-// beyond the top edge (or masked with +inf) get the trash row K+1.  A value
-// inside a guard band also goes to the trash row and sets *amb: the caller
-// recounts it after an FP64 recheck.  No branch.
-__device__ __forceinline__ unsigned row_offset(unsigned bits, unsigned lut, int shift, int base,
-                                               int top_idx, unsigned h_top, unsigned trash,
-                                               bool* amb) {
-    const int idx = min(max((int)(bits >> shift) - base, 0), top_idx);
-    const uint4 e = lds_u4(lut + 16u * (unsigned)idx);
-    const bool in_band = bits >= e.x && bits <= e.y && bits <= h_top;
-    *amb = in_band;
-    return in_band ? trash : (bits < e.x ? e.z : e.w);
+template <int HM>
+__device__ __forceinline__ void hist_add(unsigned cell, unsigned v) {
+    if (HM == kHistLane) {
+        unsigned c;
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(c) : "r"(cell) : "memory");
+        asm volatile("st.shared.b32 [%0], %1;" :: "r"(cell), "r"(c + v) : "memory");
+    } else {
+        red_add_shared(cell, v);
+    }
 }
 
-template <int HM>
-__device__ __forceinline__ void hist_inc(unsigned cell) {
-    if (HM == kHistLane) inc_shared(cell);
-    else red_add_shared(cell, 1u);
+// Table entry of an FP32 squared chord's bucket (bits >= 0: non-negative).
+__device__ __forceinline__ uint4 lut_entry(unsigned bits, unsigned lut, int shift, int base,
+                                           int top_idx) {
+    const int idx = min(max((int)(bits >> shift) - base, 0), top_idx);
+    return lds_u4(lut + 16u * (unsigned)idx);
 }
 
 // Bins NV screened values s[h R + r] (pairs of A point r and B point j + h)
-// into the thread's private histogram column at shared address col.
-template <int NT, int R, int NV, int HM>
-__device__ __forceinline__ void bin_values(const float (&s)[NV], unsigned col, unsigned lut,
-                                           int shift, int base, int top_idx, unsigned h_top,
-                                           unsigned row_bytes, int K, const Segment& S,
-                                           long long a0, long long bj,
-                                           const double* __restrict__ sC,
-                                           unsigned long long& n_recheck) {
-    const unsigned trash = (unsigned)(K + 1) * row_bytes;
-    unsigned amb_mask = 0;
+// into the thread's private histogram column at shared address col.  The
+// table gives the byte offset of the row below / above the guard band of the
+// bucket's edge; a value beyond the top edge (or masked with +inf) lands in
+// the trash row K+1.  A value inside a band is counted, for now, in the row
+// above it; the function returns true if the step held any such value, and
+// the caller then settles them (recount_band_values).  No branch.
+template <int NV, int HM>
+__device__ __forceinline__ bool bin_values(const float (&s)[NV], unsigned col, unsigned lut,
+                                           int shift, int base, int top_idx) {
+    bool any_band = false;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
-        bool amb;
-        const unsigned off = row_offset(__float_as_uint(s[v]), lut, shift, base, top_idx, h_top,
-                                        trash, &amb);
-        amb_mask |= amb ? (1u << v) : 0u;
-        hist_inc<HM>(col + off);
+        const unsigned bits = __float_as_uint(s[v]);
+        const uint4 e = lut_entry(bits, lut, shift, base, top_idx);
+        const bool below = bits < e.x;
+        any_band |= !below && bits <= e.y;
+        hist_add<HM>(col + (below ? e.z : e.w), 1u);
     }
-    // rare: values inside a guard band, recomputed in FP64 (one copy of the code)
-    while (amb_mask) {
-        const int v = __ffs(amb_mask) - 1;
-        amb_mask &= amb_mask - 1;
+    return any_band;
+}
+
+// Rare: the step held values inside a guard band.  Given the step's values
+// again, take back their provisional counts and add each to the row its FP64
+// recheck gives (one copy of the recheck code, in a loop over a bitmask).
+template <int NT, int R, int NV, int HM>
+__device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsigned col, unsigned lut,
+                                                 int shift, int base, int top_idx,
+                                                 unsigned row_bytes, int K, const Segment& S,
+                                                 long long a0, long long bj,
+                                                 const double* __restrict__ sC,
+                                                 unsigned long long& n_recheck) {
+    unsigned mask = 0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const unsigned bits = __float_as_uint(s[v]);
+        const uint4 e = lut_entry(bits, lut, shift, base, top_idx);
+        if (bits >= e.x && bits <= e.y) {
+            mask |= 1u << v;
+            hist_add<HM>(col + e.w, 0xFFFFFFFFu);  // -1
+        }
+    }
+    while (mask) {
+        const int v = __ffs(mask) - 1;
+        mask &= mask - 1;
         const unsigned slot = recheck_slot(S, a0 + (v % R) * NT, bj + v / R, sC, K);
         ++n_recheck;
-        hist_inc<HM>(col + slot * row_bytes);
+        hist_add<HM>(col + slot * row_bytes, 1u);
     }
 }
 
@@ -521,8 +540,9 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
                 const int j = jb + st * JU;
                 float s[NV];
                 chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
-                bin_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx, h_top, row_bytes, K,
-                                          S, a0, b0 + j, sC, n_recheck);
+                if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx))
+                    recount_band_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx,
+                                                       row_bytes, K, S, a0, b0 + j, sC, n_recheck);
             }
         }
         return;
@@ -535,18 +555,23 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
 
         if (HM != kHistWarp) {
             if (!(m <= hf)) continue;
-            bin_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx, h_top, row_bytes, K, S,
-                                      a0, b0 + j, sC, n_recheck);
+            if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx)) {
+                float s2[NV];
+                chords<NT, R, JU, DIAG>(s2, bxy, bz, ax, ay, az, j);
+                recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, row_bytes,
+                                                   K, S, a0, b0 + j, sC, n_recheck);
+            }
         } else {
             if (!__any_sync(0xffffffffu, m <= hf)) continue;
             const unsigned trash = (unsigned)(K + 1) * row_bytes;
             unsigned amb_mask = 0;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                bool amb;
-                const unsigned off = row_offset(__float_as_uint(s[v]), lut, shift, base, top_idx,
-                                                h_top, trash, &amb);
+                const unsigned bits = __float_as_uint(s[v]);
+                const uint4 e = lut_entry(bits, lut, shift, base, top_idx);
+                const bool amb = bits >= e.x && bits <= e.y;
                 amb_mask |= amb ? (1u << v) : 0u;
+                const unsigned off = amb ? trash : (bits < e.x ? e.z : e.w);
                 const unsigned peers = __match_any_sync(0xffffffffu, off);
                 if (lane == __ffs(peers) - 1) red_add_shared(col + off, (unsigned)__popc(peers));
             }

@@ -169,7 +169,7 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
         } else {
             // every in-range value of the bucket is rechecked in FP64; one
             // beyond the top edge (only the top bucket can hold one) is overflow
-            e[0] = 0u; e[1] = 0xFFFFFFFFu;
+            e[0] = 0u; e[1] = t->h_top;
             e[2] = (uint32_t)(K + 1); e[3] = (uint32_t)(K + 1);
             ++t->n_complex;
         }

@@ -20,7 +20,11 @@ constexpr int kMaxLut = 512;       // entries of the FP32 screening table
 //       otherwise the pair is inside an edge's guard band (or the bucket holds
 //       more than one band) and is recomputed in FP64 against c64;
 //   - slot K+1 (overflow) in the table, and any value beyond h_top, goes to a
-//     trash row that is never added to the counts.
+//     trash row that is never added to the counts;
+//   - a bucket holding several bands has {0, h_top, K+1, K+1}: all its
+//     in-range values are rechecked, values beyond h_top are overflow;
+//   - every band's upper bound is at most h_top, so a value beyond h_top is
+//     never taken for a band value.
 struct BinTable {
     int32_t K;
     uint32_t h_top;        // FP32 bits of the top edge's upper guard bound
