@@ -44,8 +44,11 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["survey", "small", "largest", "batch"],
+    ap.add_argument("--workload", choices=["survey", "small", "largest", "batch", "serve"],
                     default="survey")
+    ap.add_argument("--requests", type=int, default=2000, help="serve workload: requests")
+    ap.add_argument("--load", type=float, default=0.7,
+                    help="serve workload: offered load as a fraction of plain throughput")
     ap.add_argument("--mocks", type=int, default=256, help="batch workload: number of mocks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -439,6 +442,173 @@ def run_batch(args, rank, world, dist):
     }
 
 
+def run_serve(args, rank, world, dist):
+    """w(theta) requests with Poisson arrivals: sizes log-uniform in [1k, 2M]
+    points with 1:1 randoms, 70% auto / 30% cross, 15x15 deg patches,
+    24 log bins 1'-10 deg.  Request catalogues are random slices of
+    pre-generated clustered and uniform pools, rotated in RA (a rotation about
+    the pole keeps them equal-area and clustered).  Plain: one request at a
+    time, each count one launch, FIFO; served: the continuous-batching server
+    at the same arrival times.  Latency = done - arrival."""
+    import math
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_1208_3658_gb300 import build, synth
+    build.build()
+    from paper_1208_3658_gb300 import wtheta as W
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    nmax = 2_000_000
+    fp = synth.Patch(100.0, 15.0, 10.0, 25.0)
+    pools = {
+        "d": synth.clustered(fp, nmax, nmax // 50, 3.0, 1 + rank, "serve", "data"),
+        "r": synth.uniform(fp, nmax, 1 + rank, "serve", "random"),
+        "d2": synth.clustered(fp, nmax, nmax // 50, 3.0, 1 + rank, "serve", "data2"),
+        "r2": synth.uniform(fp, nmax, 1 + rank, "serve", "random2"),
+    }
+    e = W.wtheta_edges(1.0 / 60.0, 10.0, 24)
+    K = 24
+    rng = synth.rng_for(1 + rank, "serve", "sizes")
+    nreq = args.requests
+    sizes = np.rint(np.exp(rng.uniform(math.log(1_000), math.log(nmax), nreq))).astype(np.int64)
+    kinds = synth.rng_for(1 + rank, "serve", "kinds").random(nreq) < 0.7
+    offs = rng.integers(0, 1 << 30, (nreq, 4))
+    rot = rng.uniform(0.0, 360.0, nreq)
+
+    def cut(pool, n, off, shift):
+        a = pools[pool].reshape(-1, 2)
+        start = int(off % (nmax - n + 1))
+        out = a[start:start + n].copy()
+        out[:, 0] = np.mod(out[:, 0] + shift, 360.0)
+        return out.reshape(-1)
+
+    def materialize(q):
+        n = int(sizes[q])
+        d = cut("d", n, offs[q, 0], rot[q])
+        r = cut("r", n, offs[q, 1], rot[q])
+        if kinds[q]:
+            return d, r, None, None
+        return d, r, cut("d2", n, offs[q, 2], rot[q]), cut("r2", n, offs[q, 3], rot[q])
+
+    def pairs_of(q):
+        n = int(sizes[q])
+        return n * (n - 1) + n * n if kinds[q] else 4 * n * n
+
+    # plain: each request alone (host -> device, one launch per count, counts back)
+    stream = torch.cuda.current_stream(dev)
+    service, plain_counts = [], []
+    for q in range(nreq):
+        d, r, d2, r2 = materialize(q)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hs = [torch.from_numpy(x).pin_memory() if x is not None else None for x in (d, r, d2, r2)]
+        ds = [x.to(dev, non_blocking=True) if x is not None else None for x in hs]
+        if d2 is None:
+            c = torch.zeros((3, K + 2), dtype=torch.int64, device=dev)
+            W.wtheta_count(ds[0], None, e, True, c[0], stream=stream)
+            W.wtheta_count(ds[0], ds[1], e, False, c[1], stream=stream)
+            W.wtheta_count(ds[1], None, e, True, c[2], stream=stream)
+        else:
+            c = torch.zeros((4, K + 2), dtype=torch.int64, device=dev)
+            for k, (a, b) in enumerate([(0, 2), (0, 3), (1, 2), (1, 3)]):
+                W.wtheta_count(ds[a], ds[b], e, False, c[k], stream=stream)
+        ch = c.cpu().numpy().astype(np.uint64)
+        service.append(time.perf_counter() - t0)
+        plain_counts.append(ch)
+    total_pairs = sum(pairs_of(q) for q in range(nreq))
+    plain_rate = total_pairs / sum(service)
+    lam = args.load * plain_rate / (total_pairs / nreq)          # requests per second
+    gaps = synth.rng_for(1 + rank, "serve", "arrivals").exponential(1.0 / lam, nreq)
+    arrival = np.cumsum(gaps) - gaps[0]
+    finish, lat_plain = 0.0, []
+    for q in range(nreq):
+        finish = max(arrival[q], finish) + service[q]
+        lat_plain.append(finish - arrival[q])
+
+    # served: submit at the arrival times from a client thread
+    srv = W.wtheta_server_create(e, 120 << 30)
+    mats = [None] * nreq
+    ids = [None] * nreq
+    submit_err = []
+
+    def client():
+        t0 = time.perf_counter()
+        for q in range(nreq):
+            m = materialize(q)
+            dt = arrival[q] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            try:
+                ids[q] = W.wtheta_server_submit(srv, *m)
+            except Exception as ex:  # noqa: BLE001
+                submit_err.append(repr(ex))
+                return
+
+    launches0 = W.wtheta_kernel_launches()
+    sampler = ClockSampler()
+    sampler.start()
+    th = threading.Thread(target=client)
+    t_start = time.perf_counter()
+    th.start()
+    th.join()
+    lat_served, identical = [], True
+    t_first, t_last = None, 0.0
+    for q in range(nreq):
+        done, c, w = W.wtheta_server_wait(srv, ids[q], timeout_ms=-1)
+        info = W.wtheta_server_request_info(srv, ids[q])
+        lat_served.append(info["t_done"] - info["t_submit"])
+        t_first = info["t_submit"] if t_first is None else min(t_first, info["t_submit"])
+        t_last = max(t_last, info["t_done"])
+        identical &= bool(np.array_equal(c, plain_counts[q]))
+        W.wtheta_server_release(srv, ids[q])
+    wall = time.perf_counter() - t_start
+    clocks = sampler.stop()
+    st = W.wtheta_server_stats(srv)
+    W.wtheta_server_destroy(srv)
+    served_rate = total_pairs / (t_last - t_first)
+
+    # saturated: every request submitted at once; makespan against the plain
+    # service time of the same requests
+    srv = W.wtheta_server_create(e, 120 << 30)
+    t0 = time.perf_counter()
+    sat_ids = [W.wtheta_server_submit(srv, *materialize(q)) for q in range(nreq)]
+    for i in sat_ids:
+        W.wtheta_server_wait(srv, i, timeout_ms=-1)
+    makespan = time.perf_counter() - t0
+    W.wtheta_server_destroy(srv)
+
+    def pct(x, p):
+        return float(np.percentile(np.asarray(x), p))
+
+    return {
+        "metric": METRIC, "value": world * total_pairs / makespan, "unit": UNIT,
+        "n_gpus": world, "steps": 1, "warmup": 0, "ms_per_step": makespan * 1e3,
+        "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serve: %d Poisson requests, n log-uniform in [1k, 2M], 1:1 "
+                               "randoms, 70%% auto / 30%% cross, 15x15 deg patches, 24 log bins "
+                               "1'-10 deg, 120 GB budget, offered load %.2f of plain throughput"
+                               % (nreq, args.load),
+                   "pairs": total_pairs, "arrival_rate_hz": lam},
+        "latency_s": {"served_p50": pct(lat_served, 50), "served_p99": pct(lat_served, 99),
+                      "plain_p50": pct(lat_plain, 50), "plain_p99": pct(lat_plain, 99)},
+        "throughput": {"served_at_offered_load": served_rate,
+                       "served_saturated": total_pairs / makespan,
+                       "plain_saturated": plain_rate,
+                       "saturated_speedup": (total_pairs / makespan) / plain_rate,
+                       "note": "saturated: all requests at once, makespan incl. host copies; "
+                               "plain: sum of one-request-at-a-time service times"},
+        "counts_identical_to_plain": identical, "submit_errors": submit_err[:3],
+        "server": st, "gpu_launches": int(W.wtheta_kernel_launches() - launches0),
+        "clocks": clocks, "wall_s": wall,
+    }
+
+
 def run_reference(args, rank, world):
     """The CPU oracle on the host cores, each step a bounded sample (data rows
     against all randoms) of the same workload."""
@@ -488,8 +658,12 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
         dist_mod.init_process_group("nccl")
         dist = dist_mod
-    out = run_batch(args, rank, world, dist) if args.workload == "batch" else \
-        run_ours(args, rank, world, dist)
+    if args.workload == "batch":
+        out = run_batch(args, rank, world, dist)
+    elif args.workload == "serve":
+        out = run_serve(args, rank, world, dist)
+    else:
+        out = run_ours(args, rank, world, dist)
     if rank == 0:
         print(json.dumps(out))
     if dist is not None:

@@ -222,6 +222,93 @@ int wtheta_batch_info(const wtheta_plan* plan, wtheta_batch_info_t* info);
 int wtheta_batch_free(wtheta_plan* plan);
 
 /*
+ * Serving: w(theta) requests of different sizes, counted with continuous
+ * batching (the paper's §2.2 notes that overlapping transfers with kernels
+ * matters for larger datasets).  A scheduler thread admits requests in
+ * arrival order while their device copies fit under hbm_budget_bytes,
+ * uploads and orders them on one stream while another counts, and runs
+ * rounds: each round is one persistent pair-count launch over tile pairs of
+ * every admitted request, so a request that arrives while others are counting
+ * starts at the next round instead of waiting for them to finish.  Results
+ * do not depend on how requests were mixed (integer counts).
+ *
+ *   WTHETA_REQ_AUTO:  data, rand -> DD, DR, RR and w = Eq. 2 (wtheta_ls);
+ *   WTHETA_REQ_CROSS: data (D1), rand (R1), data2 (D2), rand2 (R2) ->
+ *                     D1D2, D1R2, R1D2, R1R2 and w (wtheta_ls_cross).
+ * Inputs are host arrays of interleaved FP64 RA/Dec degrees; submit copies
+ * them, so the caller may reuse them at once.
+ */
+#define WTHETA_REQ_AUTO 0
+#define WTHETA_REQ_CROSS 1
+
+typedef struct wtheta_request {
+    int32_t kind;
+    const double* data;
+    int64_t n_data;
+    const double* rand;
+    int64_t n_rand;
+    const double* data2;    /* cross only */
+    int64_t n_data2;
+    const double* rand2;    /* cross only */
+    int64_t n_rand2;
+} wtheta_request;
+
+/* request states reported by wtheta_server_request_info */
+#define WTHETA_RS_QUEUED 0
+#define WTHETA_RS_UPLOADING 1
+#define WTHETA_RS_COUNTING 2
+#define WTHETA_RS_FINISHING 3
+#define WTHETA_RS_DONE 4
+#define WTHETA_RS_FAILED 5
+
+typedef struct wtheta_request_info {
+    int32_t state;
+    int32_t status;           /* WTHETA_OK or the error that failed it       */
+    double t_submit;          /* seconds since the server was created        */
+    double t_admit;
+    double t_done;
+    int64_t pairs;            /* algorithmic pairs of its counts             */
+    int32_t n_counts;         /* 3 (auto) or 4 (cross)                        */
+} wtheta_request_info;
+
+typedef struct wtheta_server_stats_t {
+    int64_t rounds;           /* pair-count launches so far                   */
+    int64_t completed;        /* requests done                                */
+    int64_t queued;           /* submitted, not yet admitted                  */
+    int64_t active;           /* admitted, not yet done                       */
+    int64_t items;            /* tile pairs counted                           */
+    int64_t resident_bytes;   /* device memory held by admitted requests      */
+    int64_t kernels;          /* kernel launches issued by the scheduler      */
+} wtheta_server_stats_t;
+
+typedef struct wtheta_server wtheta_server;
+
+/* Starts a server for one edge set.  max_active: admitted requests at most
+ * (0 = 1024).  tune: kernel shape (NULL = default). */
+int wtheta_server_create(const double* bin_edges_deg, int32_t n_bins, size_t hbm_budget_bytes,
+                         int32_t max_active, const wtheta_tune* tune, wtheta_server** server);
+
+/* Queues a request; *req_id identifies it.  EBUDGET if it alone exceeds the
+ * budget, EINVAL on bad arguments (fewer than 2 points in a catalogue). */
+int wtheta_server_submit(wtheta_server* server, const wtheta_request* request, uint64_t* req_id);
+
+/* Waits up to timeout_ms (0 = just look) for a request.  *done = 1 when it
+ * has finished; then counts (host, n_counts x (K+2), may be NULL) and w (host,
+ * K, may be NULL) are written.  ETIMEOUT if timeout_ms > 0 ran out. */
+int wtheta_server_wait(wtheta_server* server, uint64_t req_id, int64_t timeout_ms, int32_t* done,
+                       uint64_t* counts, double* w);
+
+int wtheta_server_request_info(wtheta_server* server, uint64_t req_id, wtheta_request_info* info);
+
+/* Forgets a finished request (frees its host copies). */
+int wtheta_server_release(wtheta_server* server, uint64_t req_id);
+
+int wtheta_server_stats(wtheta_server* server, wtheta_server_stats_t* stats);
+
+/* Stops the scheduler, waits for the GPU, frees everything. */
+int wtheta_server_destroy(wtheta_server* server);
+
+/*
  * Allocation-free variant of wtheta_count_xyz (the paper has no counterpart).
  *
  * Some callers cannot let a library allocate device memory: a process whose

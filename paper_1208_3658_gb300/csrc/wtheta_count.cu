@@ -137,8 +137,13 @@ __device__ __forceinline__ float4 point32(double x, double y, double z, long lon
                        __int_as_float((int)idx));
 }
 
-__device__ __forceinline__ float4 sentinel32(float sign, long long k) {
-    return make_float4(sign * kSentinel * (float)(k + 1), 0.f, 0.f, 0.f);
+// Padding point k of catalogue tag t: far from the unit sphere and from the
+// padding of any other tag, (+-S (k+1), S t, 0) with the sign of t's parity;
+// its squared chord with anything else is at least S^2 >> 4, so it never
+// lands in a bin.
+__device__ __forceinline__ float4 sentinel32(int tag, long long k) {
+    const float sign = (tag & 1) ? -1.f : 1.f;
+    return make_float4(sign * kSentinel * (float)(k + 1), kSentinel * (float)tag, 0.f, 0.f);
 }
 
 // RA/Dec degrees -> FP64 unit vectors (SoA with stride xyz_stride).
@@ -157,7 +162,7 @@ __global__ void k_radec_to_xyz(const double* __restrict__ rd, long long n,
 // Caller's FP64 SoA unit vectors -> FP32 float4 copies in the same order
 // (w = index), then sentinels up to n_pad.
 __global__ void k_xyz_to_f32(const double* __restrict__ xyz, long long n, long long n_pad,
-                             float4* __restrict__ p32, float sign) {
+                             float4* __restrict__ p32, int tag) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
          i += (long long)gridDim.x * blockDim.x) {
         if (i < n) {
@@ -165,7 +170,7 @@ __global__ void k_xyz_to_f32(const double* __restrict__ xyz, long long n, long l
             check_unit(x, y, z);
             p32[i] = point32(x, y, z, i);
         } else {
-            p32[i] = sentinel32(sign, i - n);
+            p32[i] = sentinel32(tag, i - n);
         }
     }
 }
@@ -263,14 +268,14 @@ __global__ void __launch_bounds__(1024) k_scan_cells(unsigned* __restrict__ cell
 // the atomics give: counts do not depend on it.
 __global__ void k_scatter(const double* __restrict__ xyz, long long stride, long long n,
                           long long n_pad, const unsigned* __restrict__ key,
-                          unsigned* __restrict__ cell_next, float4* __restrict__ p32, float sign) {
+                          unsigned* __restrict__ cell_next, float4* __restrict__ p32, int tag) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
          i += (long long)gridDim.x * blockDim.x) {
         if (i < n) {
             const unsigned pos = atomicAdd(cell_next + key[i], 1u);
             p32[pos] = point32(xyz[i], xyz[stride + i], xyz[2 * stride + i], i);
         } else {
-            p32[i] = sentinel32(sign, i - n);
+            p32[i] = sentinel32(tag, i - n);
         }
     }
 }
@@ -287,40 +292,12 @@ __global__ void k_finalize(unsigned long long* counts, int K, unsigned long long
 // ---------------------------------------------------------------------------
 // the pair-count kernel
 // ---------------------------------------------------------------------------
-// One count: catalogue a against catalogue b (auto: a = b, pairs i < j).
-struct Segment {
-    const float4* a32;       // FP32 points (x, y, z, original index bits), tile-padded
-    const float4* b32;
-    const double* a64;       // FP64 SoA in the original order, stride a64_stride
-    const double* b64;
-    long long a64_stride, b64_stride;
-    long long tiles_a, tiles_b;
-    long long item_begin;    // first global item (tile pair) of this count
-    long long n_items;       // tile pairs of this count
-    unsigned long long* counts;  // K+2 slots (slot K+1 filled by the finalize kernel)
-    unsigned long long total;    // pairs of the count: n(n-1)/2 or n_a n_b
-    int is_auto;
-    int pad_;
-};
-
-struct PairParams {
-    Segment seg0;            // the count, when n_segs == 0
-    const Segment* segs;     // device table sorted by item_begin, when n_segs > 0
-    int n_segs;
-    int items_per_flush;     // flush the uint32 histograms after this many items
-    long long item_begin;    // this launch takes global items [item_begin, item_begin + n_items)
-    long long n_items;
-    unsigned long long* cursor;
-    unsigned long long* stats;    // WTHETA_NSTATS or null
-    BinTable tab;
-};
-
 // kHistLane: one private uint32 column per thread, plain read-modify-write;
 // kHistWarp: one column per warp, lanes with equal slots merged by
 //            __match_any_sync and added by one shared atomic;
 // kHistLaneAtomic: one private column per thread, updated by a shared atomic
 //            add (one instruction instead of load, add, store).
-enum HistMode { kHistLane = 1, kHistWarp = 2, kHistLaneAtomic = 3 };
+
 
 // Tile-pair index -> (I, J).  Auto: upper triangle I <= J, row-major.
 __device__ __forceinline__ void item_to_tiles(long long t, long long T_a, long long T_b,
@@ -646,7 +623,8 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
         }
         const Segment& S = sSeg;
         long long I, J;
-        item_to_tiles(p.item_begin + t - S.item_begin, S.tiles_a, S.tiles_b, S.is_auto, &I, &J);
+        item_to_tiles(p.item_begin + t - S.item_begin + S.item_offset, S.tiles_a, S.tiles_b,
+                      S.is_auto, &I, &J);
         const float4* gB = S.b32 + J * TB;
 #pragma unroll 4
         for (int q = 0; q < R; ++q) {
@@ -714,12 +692,6 @@ __global__ void k_finalize_segments(const Segment* __restrict__ segs, int n_segs
 // ---------------------------------------------------------------------------
 // launch plumbing
 // ---------------------------------------------------------------------------
-struct Variant {
-    int nt, r, ju, hm, def;
-    void (*kernel)(PairParams);
-    size_t (*smem)(int, int);
-};
-
 template <int NT, int R, int JU, int HM, int DEF>
 static Variant make_variant() {
     return Variant{NT, R, JU, HM, DEF, &k_pairs<NT, R, JU, HM, DEF>,
@@ -728,7 +700,7 @@ static Variant make_variant() {
 
 // Instantiated shapes (tile = threads x points_per_thread).  Per-warp
 // histograms (mode 2) need the whole warp in step, so they bin inline.
-static const Variant* variants(int* n) {
+const Variant* variants(int* n) {
     static const Variant v[] = {
         make_variant<128, 8, 2, kHistLaneAtomic, 0>(), make_variant<128, 8, 2, kHistLaneAtomic, 1>(),
         make_variant<128, 8, 2, kHistLane, 1>(),       make_variant<128, 8, 2, kHistWarp, 0>(),
@@ -740,12 +712,7 @@ static const Variant* variants(int* n) {
     return v;
 }
 
-struct DeviceInfo {
-    int sm_count = 0;
-    int max_smem_optin = 0;
-};
-
-static int device_info(DeviceInfo* out) {
+int device_info(DeviceInfo* out) {
     static std::mutex mu;
     static DeviceInfo cache[64];
     int dev = 0;
@@ -768,7 +735,7 @@ static int device_info(DeviceInfo* out) {
     return WTHETA_OK;
 }
 
-static const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, int max_smem) {
+const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, int max_smem) {
     int nv = 0;
     const Variant* v = variants(&nv);
     const int want_nt = tune && tune->threads ? tune->threads : 128;
@@ -797,7 +764,7 @@ static const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, in
     return nullptr;
 }
 
-static int grid_for(const Variant* v, size_t smem, long long n_items, int sm_count, int want_per_sm,
+int grid_for(const Variant* v, size_t smem, long long n_items, int sm_count, int want_per_sm,
                     int* grid) {
     static std::mutex mu;
     {
@@ -818,9 +785,9 @@ static int grid_for(const Variant* v, size_t smem, long long n_items, int sm_cou
     return WTHETA_OK;
 }
 
-static inline long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
+long long round_up(long long x, long long m) { return (x + m - 1) / m * m; }
 
-static int check_cuda(cudaError_t e) {
+int check_cuda(cudaError_t e) {
     if (e == cudaSuccess) return WTHETA_OK;
     if (e == cudaErrorMemoryAllocation) return WTHETA_ENOMEM;
     return WTHETA_ECUDA;
@@ -839,16 +806,7 @@ static int sort_level(long long n) {
     return L;
 }
 
-// One catalogue made ready for the pair kernel: FP64 unit vectors (the
-// caller's, or converted from RA/Dec into scratch) and spatially ordered FP32
-// copies padded to whole tiles.
-struct Prepared {
-    const float4* p32 = nullptr;
-    const double* x64 = nullptr;
-    long long stride = 0;
-};
-
-static size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
+size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
     const int L = sort_level(n);
     const size_t cells = 6ull << (2 * L);
     size_t b = (size_t)n_pad * 16 + 256;           // FP32 points
@@ -858,7 +816,7 @@ static size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
     return b;
 }
 
-static int prepare(const double* coords, long long n, long long n_pad, int is_xyz, float sign,
+int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int tag,
                    unsigned char* scratch, int sm_count, cudaStream_t st, Prepared* out) {
     const int L = sort_level(n);
     const int cells = 6 << (2 * L);
@@ -882,7 +840,7 @@ static int prepare(const double* coords, long long n, long long n_pad, int is_xy
     k_cell_count<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, L, is_xyz, key, cell);
     k_scan_cells<<<1, 1024, 0, st>>>(cell, cells);
     k_scatter<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(x64, stride, n, n_pad, key, cell, p32,
-                                                            sign);
+                                                            tag);
     count_launch(3);
     out->p32 = p32;
     out->x64 = x64;
@@ -890,14 +848,14 @@ static int prepare(const double* coords, long long n, long long n_pad, int is_xy
     return check_cuda(cudaGetLastError());
 }
 
-static unsigned long long per_item_bound(const Variant* v) {
+unsigned long long per_item_bound(const Variant* v) {
     // a thread evaluates R x TB pairs per item, so a histogram cell gains at
     // most R TB (private per-thread column) or 32 R TB (per-warp column)
     return (v->hm == kHistWarp ? 32ull : 1ull) * (unsigned long long)v->r *
            (unsigned long long)v->nt * (unsigned long long)v->r;
 }
 
-static Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
+Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
                             int is_auto, long long item_begin, unsigned long long* counts,
                             unsigned long long total) {
     Segment g;
@@ -913,7 +871,7 @@ static Segment make_segment(const Prepared& A, const Prepared& B, long long ta, 
     return g;
 }
 
-static PairParams make_params(const Variant* v, const BinTable& tab, const Segment* seg0,
+PairParams make_params(const Variant* v, const BinTable& tab, const Segment* seg0,
                               const Segment* segs, int n_segs, long long item_begin,
                               long long n_items, unsigned long long* cursor,
                               unsigned long long* stats) {
@@ -984,8 +942,8 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     unsigned char* sp = (unsigned char*)scratch;
     unsigned long long* cursor = (unsigned long long*)sp;
     Prepared A, B;
-    rc = prepare(ca, n_a, pa, is_xyz, 1.f, sp + 256, di.sm_count, st, &A);
-    if (!rc && !is_auto) rc = prepare(cb, n_b, pb, is_xyz, -1.f, sp + 256 + ba, di.sm_count, st, &B);
+    rc = prepare(ca, n_a, pa, is_xyz, 0, sp + 256, di.sm_count, st, &A);
+    if (!rc && !is_auto) rc = prepare(cb, n_b, pb, is_xyz, 1, sp + 256 + ba, di.sm_count, st, &B);
     if (is_auto) B = A;
     if (!rc) rc = check_cuda(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st));
 
@@ -1011,6 +969,22 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     if (!rc) rc = check_cuda(fe);
     return rc;
 }
+
+int launch_pairs(const Variant* v, const PairParams& prm, int grid, size_t smem,
+                 cudaStream_t st) {
+    v->kernel<<<grid, v->nt, smem, st>>>(prm);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_finalize_segments(const Segment* d_segs, int n_segs, int K, cudaStream_t st) {
+    if (n_segs <= 0) return WTHETA_OK;
+    k_finalize_segments<<<(n_segs + 127) / 128, 128, 0, st>>>(d_segs, n_segs, K);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
+void add_launches(long long n) { g_launches.fetch_add((unsigned long long)n); }
 
 // ---------------------------------------------------------------------------
 // allocation-free variant of the xyz count
@@ -1089,10 +1063,10 @@ static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double*
         return (int)std::min<long long>(std::max<long long>(g, 1), (long long)di.sm_count * 16);
     };
     // every word the kernels read is rewritten here: both padded copies and the cursor
-    k_xyz_to_f32<<<cvt_grid(pa), cvt_threads, 0, st>>>(ca, n_a, pa, a32, 1.f);
+    k_xyz_to_f32<<<cvt_grid(pa), cvt_threads, 0, st>>>(ca, n_a, pa, a32, 0);
     count_launch();
     if (!is_auto) {
-        k_xyz_to_f32<<<cvt_grid(pb), cvt_threads, 0, st>>>(cb, n_b, pb, b32, -1.f);
+        k_xyz_to_f32<<<cvt_grid(pb), cvt_threads, 0, st>>>(cb, n_b, pb, b32, 1);
         count_launch();
     }
     if ((rc = check_cuda(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st)))) return rc;
@@ -1195,10 +1169,10 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
     P->d_cursor = (unsigned long long*)base;
     P->prep.assign(2 * nc, Prepared());
     for (int m = 0; m < nc; ++m) {
-        rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], 0, 1.f, base + off[2 * m],
+        rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], 0, 0, base + off[2 * m],
                      sm_count, st, &P->prep[2 * m]);
         if (!rc)
-            rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, -1.f,
+            rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, 1,
                          base + off[2 * m + 1], sm_count, st, &P->prep[2 * m + 1]);
         if (rc) return rc;
     }
@@ -1304,10 +1278,10 @@ static int plan_capture(wtheta_plan* P, const DeviceInfo& di) {
             Prepared a, b;
             const size_t off_a = (size_t)((const unsigned char*)P->prep[2 * m].p32 - base);
             const size_t off_b = (size_t)((const unsigned char*)P->prep[2 * m + 1].p32 - base);
-            rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], 0, 1.f, base + off_a,
+            rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], 0, 0, base + off_a,
                          di.sm_count, cs, &a);
             if (!rc)
-                rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, -1.f,
+                rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, 1,
                              base + off_b, di.sm_count, cs, &b);
         }
         const size_t nbytes = (size_t)P->n_cats * 3 * (P->K + 2) * sizeof(unsigned long long);

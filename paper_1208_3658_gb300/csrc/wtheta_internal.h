@@ -1,5 +1,7 @@
 // Internal declarations shared by the library's host and device sources.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -35,6 +37,81 @@ struct BinTable {
     double c64[kMaxBins + 1];            // FP64 squared-chord edges
     uint32_t lut[kMaxLut][4];            // {lo_bits, hi_bits, slot_below, slot_above}
 };
+
+
+enum HistMode { kHistLane = 1, kHistWarp = 2, kHistLaneAtomic = 3 };
+
+// One count: catalogue a against catalogue b (auto: a = b, pairs i < j).
+struct Segment {
+    const float4* a32;       // FP32 points (x, y, z, original index bits), tile-padded
+    const float4* b32;
+    const double* a64;       // FP64 SoA in the original order, stride a64_stride
+    const double* b64;
+    long long a64_stride, b64_stride;
+    long long tiles_a, tiles_b;
+    long long item_begin;    // first global item (tile pair) of this count
+    long long n_items;       // tile pairs of this count
+    unsigned long long* counts;  // K+2 slots (slot K+1 filled by the finalize kernel)
+    unsigned long long total;    // pairs of the count: n(n-1)/2 or n_a n_b
+    long long item_offset;   // item of the count that global item item_begin is
+    int is_auto;
+    int pad_;
+};
+
+struct PairParams {
+    Segment seg0;            // the count, when n_segs == 0
+    const Segment* segs;     // device table sorted by item_begin, when n_segs > 0
+    int n_segs;
+    int items_per_flush;     // flush the uint32 histograms after this many items
+    long long item_begin;    // this launch takes global items [item_begin, item_begin + n_items)
+    long long n_items;
+    unsigned long long* cursor;
+    unsigned long long* stats;    // WTHETA_NSTATS or null
+    BinTable tab;
+};
+
+struct Variant {
+    int nt, r, ju, hm, def;
+    void (*kernel)(PairParams);
+    size_t (*smem)(int, int);
+};
+
+struct DeviceInfo {
+    int sm_count = 0;
+    int max_smem_optin = 0;
+};
+
+// One catalogue made ready for the pair kernel: FP64 unit vectors (the
+// caller's, or converted from RA/Dec into scratch) and spatially ordered FP32
+// copies padded to whole tiles.
+struct Prepared {
+    const float4* p32 = nullptr;
+    const double* x64 = nullptr;
+    long long stride = 0;
+};
+
+// Host-side launch plumbing (wtheta_count.cu), shared by the single-count,
+// batched and serving paths.
+int device_info(DeviceInfo* out);
+const Variant* variants(int* n);
+const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, int max_smem);
+int grid_for(const Variant* v, size_t smem, long long n_items, int sm_count, int want_per_sm,
+             int* grid);
+long long round_up(long long x, long long m);
+int check_cuda(cudaError_t e);
+size_t prepare_bytes(long long n, long long n_pad, int is_xyz);
+int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int tag,
+            unsigned char* scratch, int sm_count, cudaStream_t st, Prepared* out);
+unsigned long long per_item_bound(const Variant* v);
+Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
+                     int is_auto, long long item_begin, unsigned long long* counts,
+                     unsigned long long total);
+PairParams make_params(const Variant* v, const BinTable& tab, const Segment* seg0,
+                       const Segment* segs, int n_segs, long long item_begin, long long n_items,
+                       unsigned long long* cursor, unsigned long long* stats);
+int launch_pairs(const Variant* v, const PairParams& prm, int grid, size_t smem, cudaStream_t st);
+int launch_finalize_segments(const Segment* d_segs, int n_segs, int K, cudaStream_t st);
+void add_launches(long long n);
 
 // Host-side helpers (wtheta_host.cpp).
 int validate_edges(const double* edges_deg, int K);

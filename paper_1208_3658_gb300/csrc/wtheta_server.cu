@@ -1,0 +1,536 @@
+// Serving w(theta) requests with continuous batching.
+//
+// A request is one w(theta): DD, DR, RR of a data catalogue and its randoms
+// (Eq. 2), or the four counts of a cross-correlation between two catalogues
+// and their randoms.  A scheduler thread owns the GPU work:
+//   - admission: requests wait in arrival order until their device copies fit
+//     under the memory budget; an admitted request is uploaded and put in
+//     spatial order on an upload stream, overlapping the counting;
+//   - rounds: one persistent pair-count launch over a segment table drawn from
+//     every admitted, ready request (the oldest gets up to half of the round's
+//     tile pairs, the rest is shared fairly); a request that arrives while
+//     others are counting joins the next round instead of queueing behind them;
+//   - completion: after the round that holds a request's last tile pairs, the
+//     overflow slots and the copy of its counts to the host are queued on the
+//     same stream, so its counts are final when its event fires; w(theta) is
+//     then evaluated on the host.
+// There is no device-side wait on host data: every round is an ordinary
+// launch.  Host waits (wtheta_server_wait) are bounded by the caller's timeout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "wtheta_internal.h"
+
+namespace {
+
+using namespace wtheta;
+using Clock = std::chrono::steady_clock;
+
+enum ReqState { kQueued = 0, kUploading = 1, kCounting = 2, kFinishing = 3, kDone = 4, kFailed = 5 };
+
+struct Request {
+    uint64_t id = 0;
+    int kind = 0;                      // WTHETA_REQ_AUTO or WTHETA_REQ_CROSS
+    int ncat = 0;                      // 2 or 4
+    int ncount = 0;                    // 3 or 4
+    long long n[4] = {0, 0, 0, 0};
+    double* host_in[4] = {nullptr, nullptr, nullptr, nullptr};  // pinned copies
+    size_t dev_bytes = 0;
+    void* dmem = nullptr;
+    Prepared prep[4];
+    unsigned long long* d_counts = nullptr;      // ncount x (K+2)
+    Segment* d_segs = nullptr;                   // the request's counts, for finalize
+    Segment seg[4];                              // templates (item_offset = 0)
+    long long sched[4] = {0, 0, 0, 0};           // tile pairs handed to rounds so far
+    unsigned long long* host_counts = nullptr;   // pinned, ncount x (K+2)
+    cudaEvent_t ready = nullptr, finished = nullptr;
+    int state = kQueued;
+    int status = WTHETA_OK;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    std::vector<double> w;
+    long long pairs = 0;
+};
+
+struct Round {
+    Segment* d_segs = nullptr;
+    Segment* h_segs = nullptr;     // pinned staging of the table
+    int cap = 0;
+    unsigned long long* d_cursor = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+};
+
+}  // namespace
+
+struct wtheta_server {
+    int dev = 0;
+    int K = 0;
+    BinTable tab;
+    const Variant* v = nullptr;
+    size_t smem = 0;
+    int grid = 0;
+    int sm_count = 0;
+    size_t budget = 0;
+    size_t resident = 0;
+    long long round_items = 0;
+    int max_active = 0;
+    cudaStream_t up = nullptr, comp = nullptr;
+    Round rounds[2];
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<Request*> queue;
+    std::vector<Request*> active;
+    std::map<uint64_t, Request*> all;
+    uint64_t next_id = 1;
+    bool stop = false;
+    std::thread worker;
+    Clock::time_point t0;
+    // statistics
+    long long n_rounds = 0, n_done = 0, items_done = 0, kernels = 0;
+    double busy_s = 0;
+};
+
+namespace {
+
+double now_s(const wtheta_server* S) {
+    return std::chrono::duration<double>(Clock::now() - S->t0).count();
+}
+
+size_t request_bytes(const wtheta_server* S, const Request* r) {
+    const long long T = (long long)S->v->nt * S->v->r;
+    size_t b = 0;
+    for (int c = 0; c < r->ncat; ++c)
+        b += (prepare_bytes(r->n[c], round_up(r->n[c], T), 0) + 255) / 256 * 256;
+    b += (size_t)r->ncount * (S->K + 2) * 8 + 256;    // counts
+    b += sizeof(Segment) * 4 + 256;                    // the request's segment table
+    return b;
+}
+
+void free_host(Request* r) {
+    for (int c = 0; c < 4; ++c)
+        if (r->host_in[c]) {
+            cudaFreeHost(r->host_in[c]);
+            r->host_in[c] = nullptr;
+        }
+    if (r->host_counts) {
+        cudaFreeHost(r->host_counts);
+        r->host_counts = nullptr;
+    }
+    if (r->ready) cudaEventDestroy(r->ready);
+    if (r->finished) cudaEventDestroy(r->finished);
+    r->ready = r->finished = nullptr;
+}
+
+// Admission: device memory from the stream-ordered pool on the upload
+// stream, copies in, conversion and spatial ordering, counts zeroed.
+int admit(wtheta_server* S, Request* r) {
+    const long long T = (long long)S->v->nt * S->v->r;
+    int rc = check_cuda(cudaMallocAsync(&r->dmem, r->dev_bytes, S->up));
+    if (rc) return rc;
+    unsigned char* p = (unsigned char*)r->dmem;
+    r->d_counts = (unsigned long long*)p;
+    p += ((size_t)r->ncount * (S->K + 2) * 8 + 255) / 256 * 256;
+    r->d_segs = (Segment*)p;
+    p += (sizeof(Segment) * 4 + 255) / 256 * 256;
+    for (int c = 0; c < r->ncat && !rc; ++c) {
+        const long long np = round_up(r->n[c], T);
+        const size_t pb = (prepare_bytes(r->n[c], np, 0) + 255) / 256 * 256;
+        // The raw RA/Dec (16 B/pt) is uploaded into the start of the region,
+        // where the FP32 copies (16 B/pt, tile-padded) will go: the conversion
+        // reads it into the FP64 area before, in stream order, the spatial
+        // scatter overwrites it with the FP32 copies.
+        unsigned char* region = p;
+        p += pb;
+        rc = check_cuda(cudaMemcpyAsync(region, r->host_in[c], (size_t)r->n[c] * 16,
+                                        cudaMemcpyHostToDevice, S->up));
+        if (rc) break;
+        rc = prepare((const double*)region, r->n[c], np, 0, c, region,
+                     S->sm_count, S->up, &r->prep[c]);
+    }
+    if (!rc) rc = check_cuda(cudaMemsetAsync(r->d_counts, 0, (size_t)r->ncount * (S->K + 2) * 8, S->up));
+    if (rc) return rc;
+    // the counts of the request
+    auto tiles = [&](int c) { return round_up(r->n[c], T) / T; };
+    auto pairs_of = [&](int a, int b, bool aut) -> unsigned long long {
+        return aut ? (unsigned long long)r->n[a] * (unsigned long long)(r->n[a] - 1) / 2
+                   : (unsigned long long)r->n[a] * (unsigned long long)r->n[b];
+    };
+    const int K2 = S->K + 2;
+    if (r->kind == WTHETA_REQ_AUTO) {
+        r->seg[0] = make_segment(r->prep[0], r->prep[0], tiles(0), tiles(0), 1, 0, r->d_counts, pairs_of(0, 0, true));
+        r->seg[1] = make_segment(r->prep[0], r->prep[1], tiles(0), tiles(1), 0, 0, r->d_counts + K2, pairs_of(0, 1, false));
+        r->seg[2] = make_segment(r->prep[1], r->prep[1], tiles(1), tiles(1), 1, 0, r->d_counts + 2 * K2, pairs_of(1, 1, true));
+    } else {
+        // catalogues: 0 = D1, 1 = R1, 2 = D2, 3 = R2; counts D1D2, D1R2, R1D2, R1R2
+        r->seg[0] = make_segment(r->prep[0], r->prep[2], tiles(0), tiles(2), 0, 0, r->d_counts, pairs_of(0, 2, false));
+        r->seg[1] = make_segment(r->prep[0], r->prep[3], tiles(0), tiles(3), 0, 0, r->d_counts + K2, pairs_of(0, 3, false));
+        r->seg[2] = make_segment(r->prep[1], r->prep[2], tiles(1), tiles(2), 0, 0, r->d_counts + 2 * K2, pairs_of(1, 2, false));
+        r->seg[3] = make_segment(r->prep[1], r->prep[3], tiles(1), tiles(3), 0, 0, r->d_counts + 3 * K2, pairs_of(1, 3, false));
+    }
+    r->pairs = 0;
+    for (int k = 0; k < r->ncount; ++k) r->pairs += (long long)r->seg[k].total;
+    rc = check_cuda(cudaMemcpyAsync(r->d_segs, r->seg, sizeof(Segment) * r->ncount,
+                                    cudaMemcpyHostToDevice, S->up));
+    if (!rc) rc = check_cuda(cudaEventRecord(r->ready, S->up));
+    return rc;
+}
+
+long long remaining(const Request* r) {
+    long long x = 0;
+    for (int k = 0; k < r->ncount; ++k) x += r->seg[k].n_items - r->sched[k];
+    return x;
+}
+
+// Builds and launches one round on the compute stream; returns true if it
+// launched one.  Called with the server lock held.
+bool launch_round(wtheta_server* S, Round& R) {
+    std::vector<Request*> ready;
+    for (Request* r : S->active)
+        if (r->state == kCounting && remaining(r) > 0) ready.push_back(r);
+        else if (r->state == kUploading && cudaEventQuery(r->ready) == cudaSuccess) {
+            r->state = kCounting;
+            if (remaining(r) > 0) ready.push_back(r);
+        }
+    if (ready.empty()) return false;
+    // the oldest request takes up to half of the round (so a large request
+    // that has waited longest keeps moving), the rest is shared fairly, and
+    // leftovers go to whoever still has work
+    long long budget = S->round_items;
+    std::vector<long long> give(ready.size(), 0);
+    give[0] = std::min(remaining(ready[0]), budget / 2);
+    budget -= give[0];
+    while (budget > 0) {
+        long long want = 0;
+        for (size_t i = 0; i < ready.size(); ++i) want += remaining(ready[i]) - give[i] > 0;
+        if (!want) break;
+        const long long share = std::max<long long>(1, budget / want);
+        bool any = false;
+        for (size_t i = 0; i < ready.size() && budget > 0; ++i) {
+            const long long left = remaining(ready[i]) - give[i];
+            if (left <= 0) continue;
+            const long long g = std::min(left, std::min(share, budget));
+            give[i] += g;
+            budget -= g;
+            any = true;
+        }
+        if (!any) break;
+    }
+    // segment table of the round
+    int n = 0;
+    long long items = 0;
+    std::vector<Request*> finishing;
+    for (size_t i = 0; i < ready.size() && n < R.cap; ++i) {
+        Request* r = ready[i];
+        long long g = give[i];
+        for (int k = 0; k < r->ncount && g > 0 && n < R.cap; ++k) {
+            const long long left = r->seg[k].n_items - r->sched[k];
+            if (left <= 0) continue;
+            const long long take = std::min(left, g);
+            Segment sg = r->seg[k];
+            sg.item_begin = items;
+            sg.n_items = take;
+            sg.item_offset = r->sched[k];
+            R.h_segs[n++] = sg;
+            r->sched[k] += take;
+            items += take;
+            g -= take;
+        }
+        if (remaining(r) == 0) finishing.push_back(r);
+    }
+    if (n == 0) return false;
+    // every request in the round must be ready on the compute stream
+    for (Request* r : ready) cudaStreamWaitEvent(S->comp, r->ready, 0);
+    int rc = check_cuda(cudaMemcpyAsync(R.d_segs, R.h_segs, sizeof(Segment) * n,
+                                        cudaMemcpyHostToDevice, S->comp));
+    if (!rc) rc = check_cuda(cudaMemsetAsync(R.d_cursor, 0, 8, S->comp));
+    const int grid = (int)std::min<long long>(S->grid, items);
+    const PairParams prm = make_params(S->v, S->tab, nullptr, R.d_segs, n, 0, items, R.d_cursor,
+                                       nullptr);
+    if (!rc) rc = launch_pairs(S->v, prm, grid, S->smem, S->comp);
+    ++S->kernels;
+    // requests whose last tile pairs are in this round: overflow slots, then
+    // their counts to the host, in stream order after the round
+    for (Request* r : finishing) {
+        if (!rc) rc = launch_finalize_segments(r->d_segs, r->ncount, S->K, S->comp);
+        ++S->kernels;
+        if (!rc)
+            rc = check_cuda(cudaMemcpyAsync(r->host_counts, r->d_counts,
+                                            (size_t)r->ncount * (S->K + 2) * 8,
+                                            cudaMemcpyDeviceToHost, S->comp));
+        if (!rc) rc = check_cuda(cudaFreeAsync(r->dmem, S->comp));
+        if (!rc) r->dmem = nullptr;
+        if (!rc) rc = check_cuda(cudaEventRecord(r->finished, S->comp));
+        r->state = rc ? kFailed : kFinishing;
+        r->status = rc;
+    }
+    if (!rc) rc = check_cuda(cudaEventRecord(R.done, S->comp));
+    R.busy = !rc;
+    ++S->n_rounds;
+    S->items_done += items;
+    return !rc;
+}
+
+void finish_request(wtheta_server* S, Request* r) {
+    r->t_done = now_s(S);
+    r->state = kDone;
+    S->resident -= r->dev_bytes;
+    r->w.assign(S->K, 0.0);
+    const uint64_t* c = (const uint64_t*)r->host_counts;
+    const int K2 = S->K + 2;
+    if (r->kind == WTHETA_REQ_AUTO)
+        r->status = wtheta_ls(c, c + K2, c + 2 * K2, r->n[0], r->n[1], S->K, r->w.data());
+    else
+        r->status = wtheta_ls_cross(c, c + K2, c + 2 * K2, c + 3 * K2, r->n[0], r->n[2], r->n[1],
+                                    r->n[3], S->K, r->w.data());
+    ++S->n_done;
+}
+
+void worker_loop(wtheta_server* S) {
+    cudaSetDevice(S->dev);
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop) {
+        bool progressed = false;
+        // admission, in arrival order, while the budget allows
+        while (!S->queue.empty() && (int)S->active.size() < S->max_active) {
+            Request* r = S->queue.front();
+            if (S->resident + r->dev_bytes > S->budget) break;
+            S->queue.pop_front();
+            r->t_admit = now_s(S);
+            const int rc = admit(S, r);
+            if (rc) {
+                r->state = kFailed;
+                r->status = rc;
+                r->t_done = now_s(S);
+                S->cv_done.notify_all();
+                continue;
+            }
+            S->resident += r->dev_bytes;
+            r->state = kUploading;
+            S->active.push_back(r);
+            progressed = true;
+        }
+        // finished rounds free their slot
+        for (Round& R : S->rounds)
+            if (R.busy && cudaEventQuery(R.done) == cudaSuccess) {
+                R.busy = false;
+                progressed = true;
+            }
+        // completed requests
+        for (size_t i = 0; i < S->active.size();) {
+            Request* r = S->active[i];
+            if ((r->state == kFinishing && cudaEventQuery(r->finished) == cudaSuccess) ||
+                r->state == kFailed) {
+                if (r->state == kFinishing) finish_request(S, r);
+                else r->t_done = now_s(S);
+                S->active.erase(S->active.begin() + i);
+                S->cv_done.notify_all();
+                progressed = true;
+            } else {
+                ++i;
+            }
+        }
+        // keep two rounds in flight
+        for (Round& R : S->rounds)
+            if (!R.busy && launch_round(S, R)) progressed = true;
+        if (!progressed) S->cv_work.wait_for(lk, std::chrono::microseconds(200));
+    }
+}
+
+int server_create(const double* edges, int K, size_t budget, int max_active,
+                  const wtheta_tune* tune, wtheta_server** out) {
+    if (!out || budget == 0 || max_active < 0) return WTHETA_EINVAL;
+    wtheta_server* S = new wtheta_server();
+    int rc = build_table(edges, K, &S->tab);
+    DeviceInfo di;
+    if (!rc) rc = device_info(&di);
+    if (!rc) rc = check_cuda(cudaGetDevice(&S->dev));
+    if (!rc) {
+        S->K = K;
+        S->budget = budget;
+        S->max_active = max_active ? max_active : 1024;
+        S->sm_count = di.sm_count;
+        S->v = pick_variant(tune, K, S->tab.n_lut, di.max_smem_optin);
+        if (!S->v) rc = WTHETA_EINVAL;
+    }
+    if (!rc) {
+        S->smem = S->v->smem(K, S->tab.n_lut);
+        rc = grid_for(S->v, S->smem, 1LL << 40, di.sm_count, 0, &S->grid);
+        // a round of ~48 tile pairs per CTA (about 10 ms of work): short
+        // enough for new requests to join soon, long enough that the tail of
+        // each launch stays small
+        S->round_items = 48LL * S->grid;
+    }
+    if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&S->up, cudaStreamNonBlocking));
+    if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&S->comp, cudaStreamNonBlocking));
+    for (Round& R : S->rounds) {
+        if (rc) break;
+        R.cap = 4096;
+        rc = check_cuda(cudaMalloc(&R.d_segs, sizeof(Segment) * R.cap));
+        if (!rc) rc = check_cuda(cudaMallocHost(&R.h_segs, sizeof(Segment) * R.cap));
+        if (!rc) rc = check_cuda(cudaMalloc(&R.d_cursor, 8));
+        if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&R.done, cudaEventDisableTiming));
+    }
+    if (rc) {
+        delete S;
+        return rc;
+    }
+    S->t0 = Clock::now();
+    S->worker = std::thread(worker_loop, S);
+    *out = S;
+    return WTHETA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wtheta_server_create(const double* bin_edges_deg, int32_t n_bins, size_t hbm_budget_bytes,
+                         int32_t max_active, const wtheta_tune* tune, wtheta_server** server) {
+    return server_create(bin_edges_deg, n_bins, hbm_budget_bytes, max_active, tune, server);
+}
+
+int wtheta_server_submit(wtheta_server* S, const wtheta_request* q, uint64_t* req_id) {
+    if (!S || !q || !req_id) return WTHETA_EINVAL;
+    if (q->kind != WTHETA_REQ_AUTO && q->kind != WTHETA_REQ_CROSS) return WTHETA_EINVAL;
+    Request* r = new Request();
+    r->kind = q->kind;
+    r->ncat = q->kind == WTHETA_REQ_AUTO ? 2 : 4;
+    r->ncount = q->kind == WTHETA_REQ_AUTO ? 3 : 4;
+    const double* src[4] = {q->data, q->rand, q->data2, q->rand2};
+    const long long n[4] = {q->n_data, q->n_rand, q->n_data2, q->n_rand2};
+    int rc = WTHETA_OK;
+    for (int c = 0; c < r->ncat; ++c)
+        if (!src[c] || n[c] < 2) rc = WTHETA_EINVAL;
+    if (!rc) {
+        for (int c = 0; c < r->ncat; ++c) r->n[c] = n[c];
+        r->dev_bytes = request_bytes(S, r);
+        if (r->dev_bytes > S->budget) rc = WTHETA_EBUDGET;
+    }
+    // the server keeps its own pinned copies of the inputs
+    for (int c = 0; c < r->ncat && !rc; ++c) {
+        rc = check_cuda(cudaMallocHost(&r->host_in[c], (size_t)n[c] * 16));
+        if (!rc) std::memcpy(r->host_in[c], src[c], (size_t)n[c] * 16);
+    }
+    if (!rc) rc = check_cuda(cudaMallocHost(&r->host_counts, (size_t)r->ncount * (S->K + 2) * 8));
+    if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming));
+    if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&r->finished, cudaEventDisableTiming));
+    if (rc) {
+        free_host(r);
+        delete r;
+        return rc;
+    }
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        r->id = S->next_id++;
+        r->t_submit = now_s(S);
+        S->all[r->id] = r;
+        S->queue.push_back(r);
+    }
+    S->cv_work.notify_one();
+    *req_id = r->id;
+    return WTHETA_OK;
+}
+
+int wtheta_server_wait(wtheta_server* S, uint64_t id, int64_t timeout_ms, int32_t* done,
+                       uint64_t* counts, double* w) {
+    if (!S || !done) return WTHETA_EINVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return WTHETA_EINVAL;
+    Request* r = it->second;
+    const auto deadline = Clock::now() + std::chrono::milliseconds(std::max<int64_t>(timeout_ms, 0));
+    while (r->state != kDone && r->state != kFailed) {
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout &&
+            r->state != kDone && r->state != kFailed) {
+            *done = 0;
+            return timeout_ms > 0 ? WTHETA_ETIMEOUT : WTHETA_OK;
+        }
+    }
+    *done = 1;
+    if (r->state == kFailed) return r->status ? r->status : WTHETA_ECUDA;
+    if (counts) std::memcpy(counts, r->host_counts, (size_t)r->ncount * (S->K + 2) * 8);
+    if (w) std::memcpy(w, r->w.data(), sizeof(double) * S->K);
+    return r->status;
+}
+
+int wtheta_server_request_info(wtheta_server* S, uint64_t id, wtheta_request_info* info) {
+    if (!S || !info) return WTHETA_EINVAL;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return WTHETA_EINVAL;
+    const Request* r = it->second;
+    info->state = r->state;
+    info->status = r->status;
+    info->t_submit = r->t_submit;
+    info->t_admit = r->t_admit;
+    info->t_done = r->t_done;
+    info->pairs = r->pairs;
+    info->n_counts = r->ncount;
+    return WTHETA_OK;
+}
+
+int wtheta_server_release(wtheta_server* S, uint64_t id) {
+    if (!S) return WTHETA_EINVAL;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return WTHETA_EINVAL;
+    Request* r = it->second;
+    if (r->state != kDone && r->state != kFailed) return WTHETA_EINVAL;
+    free_host(r);
+    delete r;
+    S->all.erase(it);
+    return WTHETA_OK;
+}
+
+int wtheta_server_stats(wtheta_server* S, wtheta_server_stats_t* st) {
+    if (!S || !st) return WTHETA_EINVAL;
+    std::lock_guard<std::mutex> g(S->mu);
+    st->rounds = S->n_rounds;
+    st->completed = S->n_done;
+    st->queued = (int64_t)S->queue.size();
+    st->active = (int64_t)S->active.size();
+    st->items = S->items_done;
+    st->resident_bytes = (int64_t)S->resident;
+    st->kernels = S->kernels;
+    return WTHETA_OK;
+}
+
+int wtheta_server_destroy(wtheta_server* S) {
+    if (!S) return WTHETA_EINVAL;
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->worker.joinable()) S->worker.join();
+    cudaSetDevice(S->dev);
+    if (S->comp) cudaStreamSynchronize(S->comp);
+    if (S->up) cudaStreamSynchronize(S->up);
+    for (auto& kv : S->all) {
+        Request* r = kv.second;
+        if (r->dmem) cudaFree(r->dmem);
+        free_host(r);
+        delete r;
+    }
+    for (Round& R : S->rounds) {
+        if (R.d_segs) cudaFree(R.d_segs);
+        if (R.h_segs) cudaFreeHost(R.h_segs);
+        if (R.d_cursor) cudaFree(R.d_cursor);
+        if (R.done) cudaEventDestroy(R.done);
+    }
+    if (S->up) cudaStreamDestroy(S->up);
+    if (S->comp) cudaStreamDestroy(S->comp);
+    delete S;
+    return WTHETA_OK;
+}
+
+}  // extern "C"

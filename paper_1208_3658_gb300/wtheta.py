@@ -55,6 +55,29 @@ class wtheta_batch_info_t(ctypes.Structure):
                 ("autotuned", ctypes.c_int32)]
 
 
+REQ_AUTO, REQ_CROSS = 0, 1
+RS_QUEUED, RS_UPLOADING, RS_COUNTING, RS_FINISHING, RS_DONE, RS_FAILED = range(6)
+
+
+class wtheta_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("data", ctypes.c_void_p), ("n_data", ctypes.c_int64),
+                ("rand", ctypes.c_void_p), ("n_rand", ctypes.c_int64),
+                ("data2", ctypes.c_void_p), ("n_data2", ctypes.c_int64),
+                ("rand2", ctypes.c_void_p), ("n_rand2", ctypes.c_int64)]
+
+
+class wtheta_request_info(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("pairs", ctypes.c_int64),
+                ("n_counts", ctypes.c_int32)]
+
+
+class wtheta_server_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("rounds", "completed", "queued", "active", "items",
+                                              "resident_bytes", "kernels")]
+
+
 def declared_functions() -> list:
     """Names of the functions include/wtheta.h declares."""
     text = open(HEADER).read()
@@ -95,6 +118,18 @@ def lib() -> ctypes.CDLL:
             L.wtheta_batch_run.argtypes = [vp, vp, vp]
             L.wtheta_batch_info.argtypes = [vp, ctypes.POINTER(wtheta_batch_info_t)]
             L.wtheta_batch_free.argtypes = [vp]
+            L.wtheta_server_create.argtypes = [dp, i32, ctypes.c_size_t, i32,
+                                               ctypes.POINTER(wtheta_tune),
+                                               ctypes.POINTER(ctypes.c_void_p)]
+            L.wtheta_server_submit.argtypes = [vp, ctypes.POINTER(wtheta_request),
+                                               ctypes.POINTER(ctypes.c_uint64)]
+            L.wtheta_server_wait.argtypes = [vp, ctypes.c_uint64, i64,
+                                             ctypes.POINTER(ctypes.c_int32), u64p, dp]
+            L.wtheta_server_request_info.argtypes = [vp, ctypes.c_uint64,
+                                                     ctypes.POINTER(wtheta_request_info)]
+            L.wtheta_server_release.argtypes = [vp, ctypes.c_uint64]
+            L.wtheta_server_stats.argtypes = [vp, ctypes.POINTER(wtheta_server_stats_t)]
+            L.wtheta_server_destroy.argtypes = [vp]
             L.wtheta_kernel_launches.argtypes = []
             L.wtheta_kernel_launches.restype = ctypes.c_uint64
             _lib = L
@@ -279,6 +314,94 @@ def wtheta_batch_free(plan: BatchPlan):
     if plan.handle:
         _check(lib().wtheta_batch_free(plan.handle), "wtheta_batch_free")
         plan.handle = None
+
+
+class Server:
+    """A wtheta_server handle (one edge set)."""
+
+    def __init__(self, handle, n_bins):
+        self.handle = handle
+        self.n_bins = n_bins
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                lib().wtheta_server_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def wtheta_server_create(edges_deg, hbm_budget_bytes: int, max_active: int = 0,
+                         tune: dict | None = None) -> Server:
+    e, ep = _host_f64(edges_deg)
+    t = _tune_struct(tune)
+    h = ctypes.c_void_p()
+    _check(lib().wtheta_server_create(ep, len(e) - 1, int(hbm_budget_bytes), int(max_active),
+                                      ctypes.byref(t) if t is not None else None, ctypes.byref(h)),
+           "wtheta_server_create")
+    return Server(h, len(e) - 1)
+
+
+def wtheta_server_submit(srv: Server, data, rand, data2=None, rand2=None) -> int:
+    """Host numpy arrays of interleaved RA/Dec; auto if data2 is None, else cross."""
+    arrs = [np.ascontiguousarray(x, np.float64) if x is not None else None
+            for x in (data, rand, data2, rand2)]
+    kind = REQ_AUTO if data2 is None else REQ_CROSS
+    q = wtheta_request(kind,
+                       arrs[0].ctypes.data, len(arrs[0]) // 2, arrs[1].ctypes.data, len(arrs[1]) // 2,
+                       arrs[2].ctypes.data if arrs[2] is not None else None,
+                       len(arrs[2]) // 2 if arrs[2] is not None else 0,
+                       arrs[3].ctypes.data if arrs[3] is not None else None,
+                       len(arrs[3]) // 2 if arrs[3] is not None else 0)
+    rid = ctypes.c_uint64()
+    _check(lib().wtheta_server_submit(srv.handle, ctypes.byref(q), ctypes.byref(rid)),
+           "wtheta_server_submit")
+    return int(rid.value)
+
+
+def wtheta_server_wait(srv: Server, req_id: int, timeout_ms: int = -1):
+    """Returns (done, counts (n_counts, K+2) uint64 or None, w or None).
+    timeout_ms < 0 waits without limit (in 1 s slices)."""
+    K = srv.n_bins
+    counts = np.zeros(4 * (K + 2), np.uint64)
+    w = np.empty(K, np.float64)
+    done = ctypes.c_int32(0)
+    while True:
+        t = 1000 if timeout_ms < 0 else timeout_ms
+        rc = lib().wtheta_server_wait(srv.handle, req_id, t, ctypes.byref(done),
+                                      _host_u64(counts)[1], _host_f64(w)[1])
+        if rc == -4 and timeout_ms < 0:
+            continue
+        _check(rc, "wtheta_server_wait")
+        break
+    if not done.value:
+        return False, None, None
+    n = wtheta_server_request_info(srv, req_id)["n_counts"]
+    return True, counts[: n * (K + 2)].reshape(n, K + 2), w
+
+
+def wtheta_server_request_info(srv: Server, req_id: int) -> dict:
+    info = wtheta_request_info()
+    _check(lib().wtheta_server_request_info(srv.handle, req_id, ctypes.byref(info)),
+           "wtheta_server_request_info")
+    return {k: getattr(info, k) for k, _ in wtheta_request_info._fields_}
+
+
+def wtheta_server_release(srv: Server, req_id: int):
+    _check(lib().wtheta_server_release(srv.handle, req_id), "wtheta_server_release")
+
+
+def wtheta_server_stats(srv: Server) -> dict:
+    st = wtheta_server_stats_t()
+    _check(lib().wtheta_server_stats(srv.handle, ctypes.byref(st)), "wtheta_server_stats")
+    return {k: getattr(st, k) for k, _ in wtheta_server_stats_t._fields_}
+
+
+def wtheta_server_destroy(srv: Server):
+    if srv.handle:
+        _check(lib().wtheta_server_destroy(srv.handle), "wtheta_server_destroy")
+        srv.handle = None
 
 
 def wtheta_count_ex(coords_a, coords_b, coords_are_xyz: bool, edges_deg, is_auto: bool, counts,

@@ -198,3 +198,16 @@ def test_batch_plan_validation_needs_no_gpu():
     assert L.wtheta_batch_plan(cats, 2, ep, 16, None, None, ctypes.byref(h)) == -1
     assert L.wtheta_batch_run(None, None, None) == -1
     assert L.wtheta_batch_free(None) == -1
+
+
+def test_server_validation_needs_no_gpu():
+    L = W.lib()
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    ep = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    h = ctypes.c_void_p()
+    assert L.wtheta_server_create(ep, 16, 0, 0, None, ctypes.byref(h)) == -1   # zero budget
+    assert L.wtheta_server_create(ep, 16, 1 << 30, -1, None, ctypes.byref(h)) == -1
+    assert L.wtheta_server_submit(None, None, None) == -1
+    assert L.wtheta_server_destroy(None) == -1
+    d = ctypes.c_int32()
+    assert L.wtheta_server_wait(None, 1, 0, ctypes.byref(d), None, None) == -1
