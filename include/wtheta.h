@@ -132,6 +132,27 @@ int wtheta_count_xyz(const double* xyz_a, int64_t n_a, const double* xyz_b,
                      int64_t n_b, const double* bin_edges_deg, int32_t n_bins,
                      int32_t is_auto, uint64_t* counts, void* stream);
 
+/*
+ * Sharding one count over several GPUs (or processes): the pair matrix is
+ * split into n_shards contiguous ranges of rows (points of catalogue a, in
+ * input order) holding equal numbers of pairs, up to one row.  A shard's
+ * counts are exact for its pairs, overflow slot included, so the counts of
+ * all shards add up (one sum-reduction of K+2 integers) to those of
+ * wtheta_count.  The paper's summary notes that a straightforward division
+ * of the data set lets the code run on clusters of independent GPUs.
+ *
+ * wtheta_shard_rows: host only; [*row_begin, *row_end) of shard (0-based).
+ * wtheta_count_shard: as wtheta_count, for the shard's pairs only: rows
+ *   [r0, r1) against all of b (cross), or, for auto counts, the pairs i < j
+ *   with i in [r0, r1).
+ */
+int wtheta_shard_rows(int64_t n_a, int64_t n_b, int32_t is_auto, int32_t shard,
+                      int32_t n_shards, int64_t* row_begin, int64_t* row_end);
+int wtheta_count_shard(const double* ra_dec_a, int64_t n_a, const double* ra_dec_b,
+                       int64_t n_b, const double* bin_edges_deg, int32_t n_bins,
+                       int32_t is_auto, int32_t shard, int32_t n_shards, uint64_t* counts,
+                       void* stream);
+
 /* Tuning knobs of the counting kernel; zero fields mean "choose". */
 typedef struct wtheta_tune {
     int32_t threads;           /* threads per block: 64, 128 or 256           */

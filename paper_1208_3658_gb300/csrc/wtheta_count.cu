@@ -280,6 +280,11 @@ __global__ void k_scatter(const double* __restrict__ xyz, long long stride, long
     }
 }
 
+// acc[k] += add[k] for the K+2 slots (combining two counts of one shard).
+__global__ void k_add_counts(unsigned long long* acc, const unsigned long long* add, int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) acc[k] += add[k];
+}
+
 // counts[K+1] = total - sum(counts[0..K]): the overflow slot.
 __global__ void k_finalize(unsigned long long* counts, int K, unsigned long long total) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -1485,6 +1490,41 @@ int wtheta_batch_free(wtheta_plan* P) {
     cudaDeviceSynchronize();
     plan_release(P);
     return WTHETA_OK;
+}
+
+int wtheta_count_shard(const double* a, int64_t n_a, const double* b, int64_t n_b,
+                       const double* edges, int32_t K, int32_t is_auto, int32_t shard,
+                       int32_t n_shards, uint64_t* counts, void* stream) {
+    int64_t r0 = 0, r1 = 0;
+    if (is_auto) {
+        if (b && b != a) return WTHETA_EINVAL;
+        if (n_b != n_a && !(b == nullptr && n_b == 0)) return WTHETA_EINVAL;
+    }
+    int rc = wtheta_shard_rows(n_a, is_auto ? n_a : n_b, is_auto, shard, n_shards, &r0, &r1);
+    if (rc) return rc;
+    if (!counts || (n_a > 0 && !a) || (!is_auto && n_b > 0 && !b)) return WTHETA_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* rows = a ? a + 2 * r0 : nullptr;
+    if (!is_auto)
+        return count_impl(rows, r1 - r0, b, n_b, 0, edges, K, 0, (unsigned long long*)counts,
+                          nullptr, nullptr, st);
+    // rows [r0, r1) of an auto count: the pairs inside the rows, plus the rows
+    // against every later point
+    rc = count_impl(rows, r1 - r0, nullptr, 0, 0, edges, K, 1, (unsigned long long*)counts,
+                    nullptr, nullptr, st);
+    if (rc || r1 >= n_a || r1 == r0) return rc;
+    unsigned long long* tmp = nullptr;
+    if ((rc = check_cuda(cudaMallocAsync(&tmp, sizeof(unsigned long long) * (K + 2), st))))
+        return rc;
+    rc = count_impl(rows, r1 - r0, a + 2 * r1, n_a - r1, 0, edges, K, 0, tmp, nullptr, nullptr,
+                    st);
+    if (!rc) {
+        k_add_counts<<<1, 64, 0, st>>>((unsigned long long*)counts, tmp, K + 2);
+        count_launch();
+        rc = check_cuda(cudaGetLastError());
+    }
+    const cudaError_t fe = cudaFreeAsync(tmp, st);
+    return rc ? rc : check_cuda(fe);
 }
 
 uint64_t wtheta_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -243,6 +243,38 @@ int wtheta_guard_band(const double* edges, int32_t K, uint32_t* lo_bits, uint32_
     return WTHETA_OK;
 }
 
+// Pairs (i, j) with first index i < r: cross r n_b; auto (i < j) r(n-1) - r(r-1)/2.
+static unsigned long long pairs_before(long long r, long long n_a, long long n_b, int is_auto) {
+    const unsigned long long R = (unsigned long long)r;
+    if (!is_auto) return R * (unsigned long long)n_b;
+    return R * (unsigned long long)(n_a - 1) - R * (R - 1) / 2;
+}
+
+int wtheta_shard_rows(int64_t n_a, int64_t n_b, int32_t is_auto, int32_t shard, int32_t n_shards,
+                      int64_t* row_begin, int64_t* row_end) {
+    if (!row_begin || !row_end || n_a < 0 || n_b < 0 || n_shards < 1 || shard < 0 ||
+        shard >= n_shards || (is_auto != 0 && is_auto != 1))
+        return WTHETA_EINVAL;
+    const unsigned long long total = pairs_before(n_a, n_a, n_b, is_auto);
+    // smallest row r with pairs_before(r) >= s * total / n_shards (exact integers)
+    auto boundary = [&](int s) -> long long {
+        if (s <= 0) return 0;
+        if (s >= n_shards) return n_a;
+        const unsigned long long target =
+            (unsigned long long)((__int128)total * s / n_shards);
+        long long lo = 0, hi = n_a;
+        while (lo < hi) {
+            const long long mid = lo + (hi - lo) / 2;
+            if (pairs_before(mid, n_a, n_b, is_auto) >= target) hi = mid;
+            else lo = mid + 1;
+        }
+        return lo;
+    };
+    *row_begin = boundary(shard);
+    *row_end = boundary(shard + 1);
+    return WTHETA_OK;
+}
+
 int wtheta_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_t nd,
               int64_t nr, int32_t K, double* w) {
     if (!DD || !DR || !RR || !w || K < 1 || K > kMaxBins || nd < 2 || nr < 2)

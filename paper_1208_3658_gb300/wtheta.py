@@ -130,6 +130,10 @@ def lib() -> ctypes.CDLL:
             L.wtheta_server_release.argtypes = [vp, ctypes.c_uint64]
             L.wtheta_server_stats.argtypes = [vp, ctypes.POINTER(wtheta_server_stats_t)]
             L.wtheta_server_destroy.argtypes = [vp]
+            L.wtheta_shard_rows.argtypes = [i64, i64, i32, i32, i32,
+                                            ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int64)]
+            L.wtheta_count_shard.argtypes = [vp, i64, vp, i64, dp, i32, i32, i32, i32, vp, vp]
             L.wtheta_kernel_launches.argtypes = []
             L.wtheta_kernel_launches.restype = ctypes.c_uint64
             _lib = L
@@ -237,6 +241,23 @@ def wtheta_count_xyz(xyz_a, xyz_b, edges_deg, is_auto: bool, counts, stream=None
     _check(lib().wtheta_count_xyz(_dev_ptr(xyz_a), na, _dev_ptr(xyz_b), nb, ep, len(e) - 1,
                                   1 if is_auto else 0, _dev_ptr(counts), _stream(stream)),
            "wtheta_count_xyz")
+
+
+def wtheta_shard_rows(n_a: int, n_b: int, is_auto: bool, shard: int, n_shards: int):
+    r0, r1 = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().wtheta_shard_rows(n_a, n_b, 1 if is_auto else 0, shard, n_shards,
+                                   ctypes.byref(r0), ctypes.byref(r1)), "wtheta_shard_rows")
+    return int(r0.value), int(r1.value)
+
+
+def wtheta_count_shard(ra_dec_a, ra_dec_b, edges_deg, is_auto: bool, shard: int, n_shards: int,
+                       counts, stream=None):
+    e, ep = _host_f64(edges_deg)
+    na = _n_points(ra_dec_a, 2)
+    nb = na if is_auto else _n_points(ra_dec_b, 2)
+    _check(lib().wtheta_count_shard(_dev_ptr(ra_dec_a), na, _dev_ptr(ra_dec_b), nb, ep,
+                                    len(e) - 1, 1 if is_auto else 0, shard, n_shards,
+                                    _dev_ptr(counts), _stream(stream)), "wtheta_count_shard")
 
 
 def wtheta_count_xyz_noalloc(xyz_a, xyz_b, edges_deg, is_auto: bool, counts, stream=None):

@@ -275,3 +275,22 @@ def test_survey_workload_full_size(W):
     assert np.array_equal(got, want)
     w = W.wtheta_ls(DD, DR, RR, nd, nr)
     assert np.all(np.isfinite(w))
+
+
+@pytest.mark.parametrize("is_auto", [True, False])
+def test_shards_sum_to_the_whole_count(W, is_auto):
+    """wtheta_count_shard over 1..4 shards adds up to wtheta_count exactly."""
+    wl = synth.small(n=20_000)
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    a = dev(wl.data)
+    b = None if is_auto else dev(wl.rand)
+    whole = torch.zeros(len(e) + 1, dtype=torch.int64, device="cuda")
+    W.wtheta_count(a, b, e, is_auto, whole)
+    for S in (1, 2, 3, 4):
+        acc = torch.zeros_like(whole)
+        for s in range(S):
+            c = torch.zeros_like(whole)
+            W.wtheta_count_shard(a, b, e, is_auto, s, S, c)
+            acc += c
+        torch.cuda.synchronize()
+        assert torch.equal(acc, whole), S
