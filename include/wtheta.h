@@ -164,6 +164,9 @@ typedef struct wtheta_tune {
     int32_t deferred;          /* 1: bin in-range pairs as they are screened;
                                   2: note screened steps, recompute and bin after */
     int32_t blocks_per_sm;     /* resident blocks per SM the grid is sized for */
+    int32_t skip_far;          /* 1: skip tile pairs that bounding caps show to lie
+                                  wholly beyond the top edge (exact: their pairs are
+                                  overflow); 2: evaluate every tile pair          */
 } wtheta_tune;
 
 /* statistics slots accumulated by wtheta_count_ex (uint64 each) */

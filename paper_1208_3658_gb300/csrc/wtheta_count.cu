@@ -324,6 +324,99 @@ __device__ __forceinline__ void item_to_tiles(long long t, long long T_a, long l
     *J = i + (t - (i * T - i * (i - 1) / 2));
 }
 
+// Bounding cap of each tile of T spatially ordered FP32 points (real points
+// are [0, n), padding after): centre = normalised FP64 sum, radius = the
+// largest angle from the centre, plus 1e-6 rad for the FP32 rounding of the
+// points (a point moves by at most ~1.1e-7 rad from its FP64 position).
+__global__ void __launch_bounds__(128) k_tile_caps(const float4* __restrict__ p32, long long n,
+                                                   int T, TileCap* __restrict__ caps) {
+    __shared__ double red[4][4];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long t0 = (long long)blockIdx.x * T;
+    const long long t1 = min(t0 + (long long)T, n);
+    double sx = 0, sy = 0, sz = 0;
+    for (long long i = t0 + tid; i < t1; i += blockDim.x) {
+        const float4 q = p32[i];
+        sx += q.x; sy += q.y; sz += q.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sx += __shfl_xor_sync(0xffffffffu, sx, o);
+        sy += __shfl_xor_sync(0xffffffffu, sy, o);
+        sz += __shfl_xor_sync(0xffffffffu, sz, o);
+    }
+    if (lane == 0) { red[warp][0] = sx; red[warp][1] = sy; red[warp][2] = sz; }
+    __syncthreads();
+    sx = red[0][0] + red[1][0] + red[2][0] + red[3][0];
+    sy = red[0][1] + red[1][1] + red[2][1] + red[3][1];
+    sz = red[0][2] + red[1][2] + red[2][2] + red[3][2];
+    const double nrm = sqrt(sx * sx + sy * sy + sz * sz);
+    const bool empty = t1 <= t0;
+    const bool spread = !(nrm > 1e-3 * (double)(t1 - t0));  // centre ill-defined: no skipping
+    const double cx = spread ? 1.0 : sx / nrm, cy = spread ? 0.0 : sy / nrm,
+                 cz = spread ? 0.0 : sz / nrm;
+    double m = 0;
+    for (long long i = t0 + tid; i < t1; i += blockDim.x) {
+        const float4 q = p32[i];
+        const double dx = cx - q.x, dy = cy - q.y, dz = cz - q.z;
+        m = fmax(m, dx * dx + dy * dy + dz * dz);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();
+    if (lane == 0) red[warp][3] = m;
+    __syncthreads();
+    if (tid == 0) {
+        m = fmax(fmax(red[0][3], red[1][3]), fmax(red[2][3], red[3][3]));
+        TileCap c;
+        c.x = cx; c.y = cy; c.z = cz;
+        c.rho = empty ? -1.0
+                      : (spread ? 4.0 : 2.0 * asin(fmin(1.0, 0.5 * sqrt(m))) + 1e-6);
+        caps[blockIdx.x] = c;
+    }
+}
+
+// Keeps the tile pairs that may hold a pair below the top edge: those whose
+// caps are closer than theta_top + margin.  The skipped ones hold only
+// overflow pairs (and empty tiles none), which the overflow slot (total minus
+// the other slots) accounts for; counts stay exact.  Kept items are appended
+// in any order (the counts do not depend on it).
+__global__ void k_cull_items(const TileCap* __restrict__ ca, const TileCap* __restrict__ cb,
+                             long long tiles_a, long long tiles_b, int is_auto, long long n_items,
+                             double theta_top, unsigned* __restrict__ list,
+                             unsigned long long* __restrict__ n_list,
+                             unsigned long long* __restrict__ stats) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_round = (n_items + 31) / 32 * 32;
+    const int lane = threadIdx.x & 31;
+    unsigned long long skipped = 0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n_round; t += stride) {
+        bool keep = false;
+        if (t < n_items) {
+            long long I, J;
+            item_to_tiles(t, tiles_a, tiles_b, is_auto, &I, &J);
+            const TileCap A = ca[I], B = cb[J];
+            if (A.rho >= 0.0 && B.rho >= 0.0) {
+                const double dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+                const double chord = sqrt(dx * dx + dy * dy + dz * dz);
+                const double theta_c = 2.0 * asin(fmin(1.0, 0.5 * chord));
+                keep = theta_c - A.rho - B.rho - 3e-6 <= theta_top;
+            }
+            skipped += keep ? 0 : 1;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, keep);
+        unsigned long long base = 0;
+        if (lane == 0 && m) base = atomicAdd(n_list, (unsigned long long)__popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) list[base + __popc(m & ((1u << lane) - 1u))] = (unsigned)t;
+    }
+    if (stats) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) skipped += __shfl_xor_sync(0xffffffffu, skipped, o);
+        if (lane == 0 && skipped) atomicAdd(stats + WTHETA_STAT_SKIPPED, skipped);
+    }
+}
+
 // FP64 recheck: the definition's squared chord and slot for the pair of
 // sorted positions (ia, jb), found in the caller's FP64 arrays through the
 // original indices kept in the FP32 copies.
@@ -594,14 +687,18 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
     // item of another count is claimed, after the block flushed its columns
     __shared__ Segment sSeg;
     __shared__ int s_seg;
+    // items of this launch: p.n_items, or fewer when a device-side pass kept
+    // only some of them (tile pairs wholly beyond the top edge are skipped)
+    const long long n_launch =
+        p.n_items_dev ? min(p.n_items, (long long)*p.n_items_dev) : p.n_items;
     unsigned long long n_recheck = 0, n_items = 0;
     int since_flush = 0, cur_seg = -2;
     for (;;) {
         if (tid == 0) {
             const long long t = (long long)atomicAdd(p.cursor, 1ull);
-            s_item = t;
+            s_item = t < n_launch ? t : p.n_items;
             int seg = -1;
-            if (t < p.n_items && p.n_segs > 0) {
+            if (t < n_launch && p.n_segs > 0) {
                 const long long g = p.item_begin + t;
                 int lo = 0, hi = p.n_segs - 1;  // last segment with item_begin <= g
                 while (lo < hi) {
@@ -628,8 +725,9 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
         }
         const Segment& S = sSeg;
         long long I, J;
-        item_to_tiles(p.item_begin + t - S.item_begin + S.item_offset, S.tiles_a, S.tiles_b,
-                      S.is_auto, &I, &J);
+        long long local = p.item_begin + t - S.item_begin + S.item_offset;
+        if (S.item_list) local = S.item_list[local];
+        item_to_tiles(local, S.tiles_a, S.tiles_b, S.is_auto, &I, &J);
         const float4* gB = S.b32 + J * TB;
 #pragma unroll 4
         for (int q = 0; q < R; ++q) {
@@ -914,7 +1012,8 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     }
     if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
                  tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
-                 tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0))
+                 tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0 ||
+                 tune->skip_far < 0 || tune->skip_far > 2))
         return WTHETA_EINVAL;
     static thread_local BinTable tab;  // large; built per call on the host
     int rc = build_table(edges, K, &tab);
@@ -943,6 +1042,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     const size_t ba = prepare_bytes(n_a, pa, is_xyz);
     const size_t bb = is_auto ? 0 : prepare_bytes(n_b, pb, is_xyz);
     void* scratch = nullptr;
+    void* cull_scratch = nullptr;
     if ((rc = check_cuda(cudaMallocAsync(&scratch, 256 + ba + bb, st)))) return rc;
     unsigned char* sp = (unsigned char*)scratch;
     unsigned long long* cursor = (unsigned long long*)sp;
@@ -954,13 +1054,46 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
 
     const long long ta = pa / T, tb = pb / T;
     const long long n_items = is_auto ? ta * (ta + 1) / 2 : ta * tb;
+    // skip tile pairs wholly beyond the top edge (their pairs are overflow)
+    const bool skip_far = (!tune || tune->skip_far != 2) && edges[K] < 180.0 && n_items > 0 &&
+                          n_items < (1LL << 32);
+    unsigned* list = nullptr;
+    unsigned long long* n_list = nullptr;
+    if (!rc && skip_far) {
+        const size_t cull_bytes = 256 + (size_t)(ta + tb) * sizeof(TileCap) + (size_t)n_items * 4;
+        void* cs = nullptr;
+        rc = check_cuda(cudaMallocAsync(&cs, cull_bytes, st));
+        if (!rc) {
+            cull_scratch = cs;
+            n_list = (unsigned long long*)cs;
+            TileCap* caps_a = (TileCap*)((unsigned char*)cs + 256);
+            TileCap* caps_b = is_auto ? caps_a : caps_a + ta;
+            list = (unsigned*)(caps_a + ta + tb);
+            rc = check_cuda(cudaMemsetAsync(n_list, 0, 8, st));
+            if (!rc) {
+                k_tile_caps<<<(unsigned)ta, 128, 0, st>>>(A.p32, n_a, (int)T, caps_a);
+                count_launch();
+                if (!is_auto) {
+                    k_tile_caps<<<(unsigned)tb, 128, 0, st>>>(B.p32, n_b, (int)T, caps_b);
+                    count_launch();
+                }
+                const double theta_top = edges[K] * (3.14159265358979323846 / 180.0);
+                k_cull_items<<<launch_grid(n_items, di.sm_count), 256, 0, st>>>(
+                    caps_a, caps_b, ta, tb, is_auto, n_items, theta_top, list, n_list, stats);
+                count_launch();
+                rc = check_cuda(cudaGetLastError());
+            }
+        }
+    }
     const size_t smem = v->smem(K, tab.n_lut);
     int grid = 0;
     const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
     if (!rc) rc = grid_for(v, smem, n_items, di.sm_count, want_per_sm, &grid);
     if (!rc) {
-        const Segment seg = make_segment(A, B, ta, tb, is_auto, 0, counts, total);
-        const PairParams prm = make_params(v, tab, &seg, nullptr, 0, 0, n_items, cursor, stats);
+        Segment seg = make_segment(A, B, ta, tb, is_auto, 0, counts, total);
+        seg.item_list = list;
+        PairParams prm = make_params(v, tab, &seg, nullptr, 0, 0, n_items, cursor, stats);
+        prm.n_items_dev = n_list;
         v->kernel<<<grid, v->nt, smem, st>>>(prm);
         count_launch();
         rc = check_cuda(cudaGetLastError());
@@ -972,6 +1105,10 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     }
     cudaError_t fe = cudaFreeAsync(scratch, st);
     if (!rc) rc = check_cuda(fe);
+    if (cull_scratch) {
+        fe = cudaFreeAsync(cull_scratch, st);
+        if (!rc) rc = check_cuda(fe);
+    }
     return rc;
 }
 
@@ -1055,7 +1192,7 @@ static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double*
         count_launch();
         return check_cuda(cudaGetLastError());
     }
-    wtheta_tune fixed = {128, 8, 0, 0, 0, 0};  // the tile of WTHETA_NOALLOC_TILE points
+    wtheta_tune fixed = {128, 8, 0, 0, 0, 0, 2};  // the tile of WTHETA_NOALLOC_TILE points
     const Variant* v = pick_variant(&fixed, K, tab.n_lut, di.max_smem_optin);
     if (!v || (long long)v->nt * v->r != T) return WTHETA_EINVAL;
 

@@ -54,8 +54,15 @@ struct Segment {
     unsigned long long* counts;  // K+2 slots (slot K+1 filled by the finalize kernel)
     unsigned long long total;    // pairs of the count: n(n-1)/2 or n_a n_b
     long long item_offset;   // item of the count that global item item_begin is
+    const unsigned* item_list;   // if set: the count's kept items (tile pairs not skipped)
     int is_auto;
     int pad_;
+};
+
+// Bounding cap of one tile of spatially ordered points: unit centre and an
+// angular radius (radians) that bounds every point's angle from the centre.
+struct TileCap {
+    double x, y, z, rho;     // rho < 0: no real point in the tile
 };
 
 struct PairParams {
@@ -65,6 +72,7 @@ struct PairParams {
     int items_per_flush;     // flush the uint32 histograms after this many items
     long long item_begin;    // this launch takes global items [item_begin, item_begin + n_items)
     long long n_items;
+    const unsigned long long* n_items_dev;  // if set: at most this many items (device count)
     unsigned long long* cursor;
     unsigned long long* stats;    // WTHETA_NSTATS or null
     BinTable tab;

@@ -40,7 +40,8 @@ class WthetaError(RuntimeError):
 class wtheta_tune(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
                 ("hist_mode", ctypes.c_int32), ("j_per_screen", ctypes.c_int32),
-                ("deferred", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("deferred", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("skip_far", ctypes.c_int32)]
 
 
 class wtheta_catalog_pair(ctypes.Structure):
@@ -276,7 +277,8 @@ def _tune_struct(tune):
         return None
     return wtheta_tune(int(tune.get("threads", 0)), int(tune.get("points_per_thread", 0)),
                        int(tune.get("hist_mode", 0)), int(tune.get("j_per_screen", 0)),
-                       int(tune.get("deferred", 0)), int(tune.get("blocks_per_sm", 0)))
+                       int(tune.get("deferred", 0)), int(tune.get("blocks_per_sm", 0)),
+                       int(tune.get("skip_far", 0)))
 
 
 class BatchPlan:
@@ -325,7 +327,8 @@ def wtheta_batch_info(plan: BatchPlan) -> dict:
     t = info.tune
     return dict(tune=dict(threads=t.threads, points_per_thread=t.points_per_thread,
                           hist_mode=t.hist_mode, j_per_screen=t.j_per_screen,
-                          deferred=t.deferred, blocks_per_sm=t.blocks_per_sm),
+                          deferred=t.deferred, blocks_per_sm=t.blocks_per_sm,
+                          skip_far=t.skip_far),
                 n_items=info.n_items, pairs=info.pairs, evaluated_pairs=info.evaluated_pairs,
                 n_counts=info.n_counts, graph_kernels=info.graph_kernels,
                 autotune_ms=info.autotune_ms, autotuned=bool(info.autotuned))

@@ -294,3 +294,27 @@ def test_shards_sum_to_the_whole_count(W, is_auto):
             acc += c
         torch.cuda.synchronize()
         assert torch.equal(acc, whole), S
+
+
+@pytest.mark.parametrize("case", ["survey_200k", "fullsky_150k", "small"])
+def test_skipping_far_tile_pairs_is_exact(W, case):
+    """Counts with tile pairs skipped by their bounding caps equal counts with
+    every tile pair evaluated, and pairs were in fact skipped."""
+    if case == "survey_200k":
+        wl = synth.survey(n=200_000)
+    elif case == "fullsky_150k":
+        wl = synth.largest(n=150_000)
+    else:
+        wl = synth.small()
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    d, r = dev(wl.data), dev(wl.rand)
+    for a, b, auto in [(d, None, True), (d, r, False), (r, None, True)]:
+        c_all = torch.zeros(len(e) + 1, dtype=torch.int64, device="cuda")
+        c_skip = torch.zeros_like(c_all)
+        st = torch.zeros(4, dtype=torch.int64, device="cuda")
+        W.wtheta_count_ex(a, b, False, e, auto, c_all, tune=dict(skip_far=2))
+        W.wtheta_count_ex(a, b, False, e, auto, c_skip, tune=dict(skip_far=1), stats=st)
+        torch.cuda.synchronize()
+        assert torch.equal(c_all, c_skip), (case, auto)
+        if case != "small":
+            assert int(st[W.STAT_SKIPPED]) > 0
