@@ -56,6 +56,8 @@ def parse_args():
                     help="threads,points_per_thread,hist_mode of the pair kernel (default: library's)")
     ap.add_argument("--no-skip-far", action="store_true",
                     help="evaluate every tile pair (no bounding-cap skipping): brute force")
+    ap.add_argument("--no-span-bins", action="store_true",
+                    help="bin every evaluated pair through the table (no per-chunk settling)")
     ap.add_argument("--n", type=int, default=0,
                     help="points per catalogue (same shape, smaller: profiling cases)")
     return ap.parse_args()
@@ -217,6 +219,8 @@ def run_ours(args, rank, world, dist):
         tune = dict(threads=t[0], points_per_thread=t[1], hist_mode=t[2])
     if args.no_skip_far:
         tune = dict(tune or {}, skip_far=2)
+    if args.no_span_bins:
+        tune = dict(tune or {}, span_bins=2)
 
     def step(evs=None):
         calls = [(d_data, None, True), (d_data, d_rand, False), (d_rand, None, True)]
@@ -320,6 +324,7 @@ def run_ours(args, rank, world, dist):
         "config": {"workload": desc, "n_data": nd, "n_rand": nr, "n_bins": K,
                    "tune": args.tune or "library default",
                    "skip_far_tile_pairs": not args.no_skip_far,
+                   "span_bins": not args.no_span_bins,
                    "pairs_per_step": pairs, "l2": "flushed between steps (512 MB write)",
                    "inputs": "resident in HBM (FP64 RA/Dec), converted inside each call",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -332,7 +337,9 @@ def run_ours(args, rank, world, dist):
                   "recheck_frac": float(st[W.STAT_RECHECK]) / max(1, float(pairs)),
                   "evaluated_over_algorithmic": float(st[W.STAT_PAIRS]) / pairs,
                   "tile_pairs_evaluated": int(st[W.STAT_TILES]),
-                  "tile_pairs_skipped": int(st[W.STAT_SKIPPED])},
+                  "tile_pairs_skipped": int(st[W.STAT_SKIPPED]),
+                  "evaluated_pairs": int(evaluated),
+                  "span_settled_pairs": int(st[W.STAT_SPAN])},
         "wall_s_timed_region": t_wall,
     }
 

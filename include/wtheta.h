@@ -167,14 +167,22 @@ typedef struct wtheta_tune {
     int32_t skip_far;          /* 1: skip tile pairs that bounding caps show to lie
                                   wholly beyond the top edge (exact: their pairs are
                                   overflow); 2: evaluate every tile pair          */
+    int32_t span_bins;         /* 1: settle a thread's A points against a chunk of
+                                  32 B points in one slot, or by one compare per pair
+                                  against a single edge, when the bounding spheres
+                                  of the two groups allow it (exact); 2: bin every
+                                  pair through the table                          */
 } wtheta_tune;
 
 /* statistics slots accumulated by wtheta_count_ex (uint64 each) */
-#define WTHETA_STAT_PAIRS 0     /* pairs evaluated, tile padding included     */
+#define WTHETA_STAT_PAIRS 0     /* pairs whose squared chord was computed,
+                                   tile padding included                      */
 #define WTHETA_STAT_RECHECK 1   /* pairs recomputed in FP64 (guard band)      */
 #define WTHETA_STAT_TILES 2     /* tile pairs evaluated                       */
 #define WTHETA_STAT_SKIPPED 3   /* tile pairs skipped as wholly out of range  */
-#define WTHETA_NSTATS 4
+#define WTHETA_STAT_SPAN 4      /* pairs settled per (A group, B chunk) span,
+                                   without a table lookup per pair            */
+#define WTHETA_NSTATS 5
 
 /*
  * wtheta_count / wtheta_count_xyz with explicit tuning and statistics.

@@ -9,9 +9,14 @@
 //   - RA/Dec -> FP64 unit vectors once per point (kept in the caller's order
 //     for the rare FP64 recheck);
 //   - the points are put in spatial order (cube-map face, then a Hilbert curve
-//     on the face; a counting sort over cells) so that a tile of consecutive
+//     on the face; a radix sort of 31-bit keys) so that a tile of consecutive
 //     points is a compact patch of sky and a warp's pairs mostly share one
 //     fate (all beyond the top edge, or all in range);
+//   - tile pairs whose bounding caps lie wholly beyond the top edge are
+//     skipped (their pairs are overflow); inside a tile pair, a thread's group
+//     of R consecutive A points and a chunk of 32 B points are settled in one
+//     slot, or by one FP32 comparison per pair against a single edge, when
+//     their bounding spheres allow it;
 //   - FP32 float4 copies (x, y, z, original index) padded to whole tiles with
 //     far-away sentinel points that never land in a bin;
 //   - a CTA stages the B tile in shared memory, negated and duplicated for
@@ -215,28 +220,95 @@ __device__ __forceinline__ unsigned cell_key(double x, double y, double z, int L
     return face * S * S + hilbert_index(S, iu, iv);
 }
 
-// Cell of every point and the number of points per cell.
-__global__ void k_cell_count(const double* __restrict__ xyz, long long stride, long long n,
-                             int L, int check, unsigned* __restrict__ key,
-                             unsigned* __restrict__ cell_count) {
+// Spatial order of a catalogue: a 31-bit key per point (cube-map face, then
+// the Hilbert index of its cell on a 2^14 x 2^14 grid of the face, cells of
+// about 20 arcsec), sorted by a stable least-significant-digit radix sort
+// (4 passes of 8 bits: per-block digit counts, one exclusive scan, a stable
+// scatter).  Consecutive points of the order are then close on the sky down
+// to the scale of a few points, which the per-tile culling and the
+// per-chunk settling of pairs both rely on.
+constexpr int kSortLevel = 14;
+constexpr int kSortThreads = 256;
+constexpr int kSortRounds = 16;
+constexpr long long kSortTile = (long long)kSortThreads * kSortRounds;  // keys per block
+
+__global__ void k_sort_keys(const double* __restrict__ xyz, long long stride, long long n,
+                            int check, unsigned* __restrict__ key, unsigned* __restrict__ idx) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
         const double x = xyz[i], y = xyz[stride + i], z = xyz[2 * stride + i];
         if (check) check_unit(x, y, z);
-        const unsigned k = cell_key(x, y, z, L);
-        key[i] = k;
-        atomicAdd(cell_count + k, 1u);
+        key[i] = cell_key(x, y, z, kSortLevel);
+        idx[i] = (unsigned)i;
     }
 }
 
-// Exclusive prefix sum of the cell counts, in place (one block of 1024).
-__global__ void __launch_bounds__(1024) k_scan_cells(unsigned* __restrict__ cell, int n_cells) {
+// hist[d * n_blocks + b] = keys of block b whose digit is d.
+__global__ void __launch_bounds__(kSortThreads) k_digit_hist(const unsigned* __restrict__ key,
+                                                             long long n, int shift,
+                                                             unsigned* __restrict__ hist) {
+    __shared__ unsigned cnt[256];
+    const int t = threadIdx.x;
+    cnt[t] = 0;
+    __syncthreads();
+    const long long lo = blockIdx.x * kSortTile, hi = min(lo + kSortTile, n);
+    for (long long i = lo + t; i < hi; i += kSortThreads) atomicAdd(&cnt[(key[i] >> shift) & 255u], 1u);
+    __syncthreads();
+    hist[(long long)t * gridDim.x + blockIdx.x] = cnt[t];
+}
+
+// Stable scatter of one pass: block b writes its keys of digit d from
+// offs[d * n_blocks + b] on, in index order (rounds of 256 keys; inside a
+// round, warps in order and lanes in order).
+__global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
+    const unsigned* __restrict__ key_in, const unsigned* __restrict__ idx_in, long long n,
+    int shift, const unsigned* __restrict__ offs, unsigned* __restrict__ key_out,
+    unsigned* __restrict__ idx_out) {
+    __shared__ unsigned base[256];
+    __shared__ unsigned wcnt[kSortThreads / 32][256];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    base[t] = offs[(long long)t * gridDim.x + blockIdx.x];
+    const long long lo = blockIdx.x * kSortTile;
+    for (int r = 0; r < kSortRounds; ++r) {
+#pragma unroll
+        for (int q = 0; q < kSortThreads / 32; ++q) wcnt[q][t] = 0;
+        __syncthreads();
+        const long long i = lo + (long long)r * kSortThreads + t;
+        const bool valid = i < n;
+        const unsigned k = valid ? key_in[i] : 0u;
+        const unsigned d = valid ? (k >> shift) & 255u : 256u;
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        {
+            unsigned acc = base[t];
+#pragma unroll
+            for (int q = 0; q < kSortThreads / 32; ++q) {
+                const unsigned c = wcnt[q][t];
+                wcnt[q][t] = acc;
+                acc += c;
+            }
+            base[t] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            const unsigned pos = wcnt[w][d] + rank;
+            key_out[pos] = k;
+            idx_out[pos] = idx_in[i];
+        }
+        __syncthreads();
+    }
+}
+
+// Exclusive prefix sum in place (one block of 1024).
+__global__ void __launch_bounds__(1024) k_exclusive_scan(unsigned* __restrict__ a, int n) {
     __shared__ unsigned warp_sum[32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int per = (n_cells + 1023) / 1024;
-    const int lo = min(t * per, n_cells), hi = min(lo + per, n_cells);
+    const int per = (n + 1023) / 1024;
+    const int lo = min(t * per, n), hi = min(lo + per, n);
     unsigned sum = 0;
-    for (int i = lo; i < hi; ++i) sum += cell[i];
+    for (int i = lo; i < hi; ++i) sum += a[i];
     unsigned incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -257,23 +329,22 @@ __global__ void __launch_bounds__(1024) k_scan_cells(unsigned* __restrict__ cell
     __syncthreads();
     unsigned run = incl - sum + (w > 0 ? warp_sum[w - 1] : 0u);
     for (int i = lo; i < hi; ++i) {
-        const unsigned c = cell[i];
-        cell[i] = run;
+        const unsigned c = a[i];
+        a[i] = run;
         run += c;
     }
 }
 
-// Places every point at its cell's next free slot (FP32 copy, w = original
-// index); slots n..n_pad-1 get sentinels.  Order inside a cell is whatever
-// the atomics give: counts do not depend on it.
-__global__ void k_scatter(const double* __restrict__ xyz, long long stride, long long n,
-                          long long n_pad, const unsigned* __restrict__ key,
-                          unsigned* __restrict__ cell_next, float4* __restrict__ p32, int tag) {
+// FP32 copies in sorted order (w = original index); slots n..n_pad-1 get
+// sentinels.
+__global__ void k_gather_points(const double* __restrict__ xyz, long long stride, long long n,
+                                long long n_pad, const unsigned* __restrict__ order,
+                                float4* __restrict__ p32, int tag) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
          i += (long long)gridDim.x * blockDim.x) {
         if (i < n) {
-            const unsigned pos = atomicAdd(cell_next + key[i], 1u);
-            p32[pos] = point32(xyz[i], xyz[stride + i], xyz[2 * stride + i], i);
+            const long long j = order[i];
+            p32[i] = point32(xyz[j], xyz[stride + j], xyz[2 * stride + j], j);
         } else {
             p32[i] = sentinel32(tag, i - n);
         }
@@ -376,6 +447,37 @@ __global__ void __launch_bounds__(128) k_tile_caps(const float4* __restrict__ p3
     }
 }
 
+// Bounding sphere of every chunk of 32 consecutive spatially ordered FP32
+// points: centre = the FP32 mean of the chunk's points, radius = the largest
+// FP32 distance of a point from it, enlarged by a relative 1e-6 for the few
+// roundings of that arithmetic.  A chunk holding a padding point gets radius
+// -1, so that its pairs are never settled per chunk.  One warp per chunk.
+__global__ void k_chunk_caps(const float4* __restrict__ p32, long long n, long long n_pad,
+                             float4* __restrict__ caps) {
+    const int lane = threadIdx.x & 31;
+    const long long n_chunks = n_pad / 32;
+    const long long wpb = blockDim.x / 32;
+    for (long long c = blockIdx.x * wpb + (threadIdx.x >> 5); c < n_chunks;
+         c += (long long)gridDim.x * wpb) {
+        const long long i = c * 32 + lane;
+        const float4 q = p32[i];
+        float sx = q.x, sy = q.y, sz = q.z;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            sx += __shfl_xor_sync(0xffffffffu, sx, o);
+            sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        }
+        const float cx = sx * (1.f / 32), cy = sy * (1.f / 32), cz = sz * (1.f / 32);
+        const float dx = q.x - cx, dy = q.y - cy, dz = q.z - cz;
+        float m = dx * dx + dy * dy + dz * dz;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        const bool pad = __any_sync(0xffffffffu, i >= n);
+        if (lane == 0) caps[c] = make_float4(cx, cy, cz, pad ? -1.f : sqrtf(m) * (1.f + 1e-6f));
+    }
+}
+
 // Keeps the tile pairs that may hold a pair below the top edge: those whose
 // caps are closer than theta_top + margin.  The skipped ones hold only
 // overflow pairs (and empty tiles none), which the overflow slot (total minus
@@ -445,6 +547,7 @@ struct PairKernel {
 
     static size_t smem_bytes(int K, int n_lut) {
         size_t b = (size_t)TB * 24;             // B tile: {-x,-x,-y,-y} + {-z,-z}
+        b += (size_t)TB / 32 * 16;              // bounding spheres of its 32-point chunks
         b += (size_t)n_lut * 16;                // screening table
         b += (size_t)(K + 2) * 8;               // FP64 edges (+ pad)
         b += (size_t)(K + 2) * HCOLS * 4;       // histograms, row K+1 a trash row
@@ -531,7 +634,7 @@ __device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsign
     while (mask) {
         const int v = __ffs(mask) - 1;
         mask &= mask - 1;
-        const unsigned slot = recheck_slot(S, a0 + (v % R) * NT, bj + v / R, sC, K);
+        const unsigned slot = recheck_slot(S, a0 + v % R, bj + v / R, sC, K);
         ++n_recheck;
         hist_add<HM>(col + slot * row_bytes, 1u);
     }
@@ -564,7 +667,7 @@ __device__ __forceinline__ void chords(float (&s)[JU * R], unsigned bxy_base, un
         for (int h = 0; h < JU; ++h)
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                if (j + h <= r * NT + (int)threadIdx.x) s[h * R + r] = __int_as_float(0x7f800000);
+                if (j + h <= (int)threadIdx.x * R + r) s[h * R + r] = __int_as_float(0x7f800000);
     }
 }
 
@@ -577,13 +680,133 @@ __device__ __forceinline__ float min_of(const float (&s)[NV]) {
     return m;
 }
 
+// The FP32 steps [j0, j1) of a B tile for the thread's R A points, each pair
+// binned through the table (values inside a guard band settled in FP64).
+template <int NT, int R, int JU, int HM, bool DIAG>
+__device__ __forceinline__ void exact_steps(int j0, int j1, unsigned bxy, unsigned bz,
+                                            unsigned lut, const double* __restrict__ sC,
+                                            unsigned col, const f2_t (&ax)[R / 2],
+                                            const f2_t (&ay)[R / 2], const f2_t (&az)[R / 2],
+                                            float hf, int shift, int base, int top_idx,
+                                            unsigned row_bytes, int K, const Segment& S,
+                                            long long a0, long long b0,
+                                            unsigned long long& n_recheck) {
+    constexpr int NV = JU * R;
+#pragma unroll 1
+    for (int j = j0; j < j1; j += JU) {
+        float s[NV];
+        chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
+        const float m = min_of(s);
+        if (!(m <= hf)) continue;
+        if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx)) {
+            float s2[NV];
+            chords<NT, R, JU, DIAG>(s2, bxy, bz, ax, ay, az, j);
+            recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, row_bytes, K,
+                                               S, a0, b0 + j, sC, n_recheck);
+        }
+    }
+}
+
+// Bounding sphere of the thread's R A points (FP32): centre = their mean,
+// radius = the largest distance from it, enlarged by a relative 1e-6 for the
+// roundings of that arithmetic.  Padding sentinels give a radius far above 2.
+template <int R>
+__device__ __forceinline__ float4 group_cap(const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
+                                            const f2_t (&az)[R / 2]) {
+    float x[R], y[R], z[R];
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) {
+        unpack2(ax[q], x[2 * q], x[2 * q + 1]);
+        unpack2(ay[q], y[2 * q], y[2 * q + 1]);
+        unpack2(az[q], z[2 * q], z[2 * q + 1]);
+    }
+    float cx = 0.f, cy = 0.f, cz = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) { cx += x[r]; cy += y[r]; cz += z[r]; }
+    cx *= 1.f / R; cy *= 1.f / R; cz *= 1.f / R;
+    float m = 0.f;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const float dx = x[r] - cx, dy = y[r] - cy, dz = z[r] - cz;
+        m = fmaxf(m, dx * dx + dy * dy + dz * dz);
+    }
+    return make_float4(cx, cy, cz, sqrtf(m) * (1.f + 1e-6f));
+}
+
+// How the pairs of a group of A points (sphere ga) with a chunk of B points
+// (sphere gb) can be settled.  By the triangle inequality every FP32 pair
+// distance lies within |ca - cb| -/+ (ra + rb); the FP64 unit vectors are
+// within 1.2e-7 of their FP32 copies and the FP32 arithmetic here errs by a
+// few units in the last place, all covered by the 1e-6 absolute and relative
+// slack, so every pair's FP64 squared chord lies in [slo, shi].  The table
+// classifies both ends (values inside a guard band or a bucket with several
+// edges are ambiguous):
+//   0  both ends in one slot: every pair is in slot rlo;
+//   1  adjacent slots split by the edge of `edge` (its guard band [x, y]):
+//      each pair is in rlo or rhi by one FP32 comparison, outside the band;
+//   2  anything else: bin pair by pair.
+__device__ __forceinline__ int span_mode(float4 ga, float4 gb, unsigned lut, int shift, int base,
+                                         int top_idx, unsigned& rlo, unsigned& rhi,
+                                         uint4& edge) {
+    const float dx = ga.x - gb.x, dy = ga.y - gb.y, dz = ga.z - gb.z;
+    const float dc = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float rr = (ga.w + gb.w) * (1.f + 1e-6f) + 1e-6f;
+    const float lo = dc * (1.f - 1e-6f) - rr, hi = dc * (1.f + 1e-6f) + rr;
+    const float slo = lo > 0.f ? lo * lo * (1.f - 1e-5f) : 0.f;
+    const float shi = hi * hi * (1.f + 1e-5f);
+    if (!(ga.w <= 2.f && gb.w >= 0.f && gb.w <= 2.f)) return 2;  // padding (or NaN)
+    const unsigned bl = __float_as_uint(slo), bh = __float_as_uint(shi);
+    const uint4 el = lut_entry(bl, lut, shift, base, top_idx);
+    const uint4 eh = lut_entry(bh, lut, shift, base, top_idx);
+    if (!(bl < el.x || bl > el.y) || !(bh < eh.x || bh > eh.y)) return 2;
+    rlo = bl < el.x ? el.z : el.w;
+    rhi = bh < eh.x ? eh.z : eh.w;
+    if (rlo == rhi) return 0;
+    if (eh.z == rlo && eh.w == rhi) { edge = eh; return 1; }
+    if (el.z == rlo && el.w == rhi) { edge = el; return 1; }
+    return 2;
+}
+
+// One step of a two-slot chunk: the squared chords of JU B points with the
+// thread's R A points, computed exactly as in chords(), then d = s - mid.
+// neg counts the values with d < 0; mb keeps the smallest |d|.
+template <int R, int JU>
+__device__ __forceinline__ void two_slot_step(unsigned bxy_base, unsigned bz_base,
+                                              const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
+                                              const f2_t (&az)[R / 2], int j, f2_t nmid,
+                                              unsigned& neg, float& mb) {
+#pragma unroll
+    for (int h = 0; h < JU; ++h) {
+        f2_t bx, by;
+        lds_f2x2(bxy_base + 16u * (unsigned)(j + h), bx, by);
+        const f2_t bz = lds_f2(bz_base + 8u * (unsigned)(j + h));
+        float m = mb;
+        unsigned c = 0;
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) {
+            const f2_t dx = add2(ax[q], bx);
+            const f2_t dy = add2(ay[q], by);
+            const f2_t dz = add2(az[q], bz);
+            const f2_t t = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+            float d0, d1;
+            unpack2(add2(t, nmid), d0, d1);
+            m = min3f(m, fabsf(d0), fabsf(d1));
+            c += (__float_as_uint(d0) >> 31) + (__float_as_uint(d1) >> 31);
+        }
+        mb = m;
+        neg += c;
+    }
+}
+
 template <int NT, int R, int JU, int HM, int DEF, bool DIAG>
-__device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lut,
+__device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lut, unsigned caps,
                                           const double* __restrict__ sC, unsigned hist,
                                           const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
                                           const f2_t (&az)[R / 2], const PairParams& p,
                                           const Segment& S, long long I, long long J,
-                                          unsigned long long& n_recheck) {
+                                          unsigned long long& n_recheck,
+                                          unsigned long long& n_span,
+                                          unsigned long long& n_skip) {
     using PK = PairKernel<NT, R, JU, HM, DEF>;
     constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
     constexpr int NV = JU * R;
@@ -593,7 +816,7 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
     const int shift = p.tab.shift, base = p.tab.base, K = p.tab.K, top_idx = p.tab.n_lut - 1;
     const unsigned row_bytes = HCOLS * 4u;
     const unsigned col = hist + 4u * (unsigned)(HM == kHistWarp ? warp : tid);
-    const long long a0 = I * TA + tid, b0 = J * TB;
+    const long long a0 = I * TA + (long long)tid * R, b0 = J * TB;
 
     if (DEF) {
         // Deferred binning: the screening loop only notes, one bit per step,
@@ -621,22 +844,12 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
             }
         }
         return;
-    } else {
+    } else if (HM == kHistWarp) {
 #pragma unroll 1
-    for (int j = 0; j < TB; j += JU) {
-        float s[NV];
-        chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
-        const float m = min_of(s);
-
-        if (HM != kHistWarp) {
-            if (!(m <= hf)) continue;
-            if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx)) {
-                float s2[NV];
-                chords<NT, R, JU, DIAG>(s2, bxy, bz, ax, ay, az, j);
-                recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, row_bytes,
-                                                   K, S, a0, b0 + j, sC, n_recheck);
-            }
-        } else {
+        for (int j = 0; j < TB; j += JU) {
+            float s[NV];
+            chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
+            const float m = min_of(s);
             if (!__any_sync(0xffffffffu, m <= hf)) continue;
             const unsigned trash = (unsigned)(K + 1) * row_bytes;
             unsigned amb_mask = 0;
@@ -653,12 +866,69 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
             while (amb_mask) {
                 const int v = __ffs(amb_mask) - 1;
                 amb_mask &= amb_mask - 1;
-                const unsigned slot = recheck_slot(S, a0 + (v % R) * NT, b0 + j + v / R, sC, K);
+                const unsigned slot = recheck_slot(S, a0 + v % R, b0 + j + v / R, sC, K);
                 ++n_recheck;
                 red_add_shared(col + slot * row_bytes, 1u);
             }
         }
+        return;
     }
+    if (DIAG || !p.span || !S.b_caps) {
+        exact_steps<NT, R, JU, HM, DIAG>(0, TB, bxy, bz, lut, sC, col, ax, ay, az, hf, shift, base,
+                                         top_idx, row_bytes, K, S, a0, b0, n_recheck);
+        return;
+    }
+    // Chunks of 32 B points: the warp bins a chunk pair by pair only if one
+    // of its threads has to; otherwise each thread settles its A points
+    // against the chunk in one slot or with one comparison per pair.
+    constexpr int CH = 32;
+    static_assert(TB % CH == 0 && CH % JU == 0, "whole chunks");
+    const float4 ga = group_cap<R>(ax, ay, az);
+#pragma unroll 1
+    for (int c0 = 0; c0 < TB; c0 += CH) {
+        const uint4 gbu = lds_u4(caps + 16u * (unsigned)(c0 / CH));
+        const float4 gb = make_float4(__uint_as_float(gbu.x), __uint_as_float(gbu.y),
+                                      __uint_as_float(gbu.z), __uint_as_float(gbu.w));
+        unsigned rlo = 0, rhi = 0;
+        uint4 edge = make_uint4(0u, 0u, 0u, 0u);
+        const int mode = span_mode(ga, gb, lut, shift, base, top_idx, rlo, rhi, edge);
+        if (__any_sync(0xffffffffu, mode == 2)) {
+            exact_steps<NT, R, JU, HM, false>(c0, c0 + CH, bxy, bz, lut, sC, col, ax, ay, az, hf,
+                                              shift, base, top_idx, row_bytes, K, S, a0, b0,
+                                              n_recheck);
+            continue;
+        }
+        if (mode == 0) {
+            hist_add<HM>(col + rlo, (unsigned)(R * CH));
+            n_span += R * CH;
+        }
+        if (__all_sync(0xffffffffu, mode == 0)) {
+            n_skip += R * CH;
+            continue;
+        }
+        // Two slots: d = s - mid with mid the middle of the edge's guard band
+        // [lo, hi] and G its half-width (both exact: the band is narrow).
+        // |d| > G puts s outside the band, and then d < 0 means below it.
+        const float lo_f = __uint_as_float(edge.x), hi_f = __uint_as_float(edge.y);
+        const float mid = 0.5f * (lo_f + hi_f);
+        const float G = fmaxf(mid - lo_f, hi_f - mid);
+        const f2_t nmid = pack2(-mid, -mid);
+        unsigned neg = 0;
+        float mb = __int_as_float(0x7f800000);
+#pragma unroll 2
+        for (int j = c0; j < c0 + CH; j += JU) two_slot_step<R, JU>(bxy, bz, ax, ay, az, j, nmid, neg, mb);
+        if (mode == 1) {
+            if (mb <= G) {
+                // rare: a value near the edge; this thread bins the chunk pair by pair
+                exact_steps<NT, R, JU, HM, false>(c0, c0 + CH, bxy, bz, lut, sC, col, ax, ay, az,
+                                                  hf, shift, base, top_idx, row_bytes, K, S, a0,
+                                                  b0, n_recheck);
+            } else {
+                hist_add<HM>(col + rlo, neg);
+                hist_add<HM>(col + rhi, (unsigned)(R * CH) - neg);
+                n_span += R * CH;
+            }
+        }
     }
 }
 
@@ -670,7 +940,8 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
     const int K = p.tab.K;
     ulonglong2* sBxy = reinterpret_cast<ulonglong2*>(smem);
     f2_t* sBz = reinterpret_cast<f2_t*>(sBxy + TB);
-    uint4* sLut = reinterpret_cast<uint4*>(sBz + TB);
+    float4* sCap = reinterpret_cast<float4*>(sBz + TB);
+    uint4* sLut = reinterpret_cast<uint4*>(sCap + TB / 32);
     double* sC = reinterpret_cast<double*>(sLut + p.tab.n_lut);
     unsigned* hist = reinterpret_cast<unsigned*>(sC + (K + 2));
     __shared__ long long s_item;
@@ -691,7 +962,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
     // only some of them (tile pairs wholly beyond the top edge are skipped)
     const long long n_launch =
         p.n_items_dev ? min(p.n_items, (long long)*p.n_items_dev) : p.n_items;
-    unsigned long long n_recheck = 0, n_items = 0;
+    unsigned long long n_recheck = 0, n_items = 0, n_span = 0, n_skip = 0;
     int since_flush = 0, cur_seg = -2;
     for (;;) {
         if (tid == 0) {
@@ -735,7 +1006,11 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
             sBxy[q * NT + tid] = make_ulonglong2(pack2(-b.x, -b.x), pack2(-b.y, -b.y));
             sBz[q * NT + tid] = pack2(-b.z, -b.z);
         }
-        // The A points are packed two by two for the FP32x2 instructions.
+        if (S.b_caps)
+            for (int q = tid; q < TB / 32; q += NT) sCap[q] = S.b_caps[J * (TB / 32) + q];
+        // The thread's A points are R consecutive points of the spatial order
+        // (a compact group: see span_mode), packed two by two for the FP32x2
+        // instructions.
         // Each value goes through an explicit add of +0 (exact; it only turns
         // -0 into +0, which leaves every squared chord unchanged): the packed
         // operands then get registers of their own instead of being formed in
@@ -745,21 +1020,21 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
         const float4* gA = S.a32 + I * TA;
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) {
-            const float4 u = gA[(2 * q) * NT + tid];
-            const float4 v = gA[(2 * q + 1) * NT + tid];
+            const float4 u = gA[tid * R + 2 * q];
+            const float4 v = gA[tid * R + 2 * q + 1];
             ax[q] = pack2(__fadd_rn(u.x, 0.f), __fadd_rn(v.x, 0.f));
             ay[q] = pack2(__fadd_rn(u.y, 0.f), __fadd_rn(v.y, 0.f));
             az[q] = pack2(__fadd_rn(u.z, 0.f), __fadd_rn(v.z, 0.f));
         }
         __syncthreads();  // B tile staged
         const unsigned a_bxy = smem_addr(sBxy), a_bz = smem_addr(sBz), a_lut = smem_addr(sLut),
-                       a_hist = smem_addr(hist);
+                       a_cap = smem_addr(sCap), a_hist = smem_addr(hist);
         if (S.is_auto && I == J)
-            tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, sC, a_hist, ax, ay, az, p, S, I,
-                                                J, n_recheck);
+            tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, a_cap, sC, a_hist, ax, ay, az,
+                                                p, S, I, J, n_recheck, n_span, n_skip);
         else
-            tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, sC, a_hist, ax, ay, az, p, S,
-                                                 I, J, n_recheck);
+            tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, a_cap, sC, a_hist, ax, ay, az,
+                                                 p, S, I, J, n_recheck, n_span, n_skip);
         ++n_items;
         if (++since_flush == p.items_per_flush) {
             __syncthreads();
@@ -771,10 +1046,19 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
     // all threads left the loop after the same barrier
     if (cur_seg != -2) flush_hist<NT, HCOLS>(hist, K, sSeg.counts);
     if (p.stats) {
-        unsigned long long v = n_recheck;
+        unsigned long long v = n_recheck, sp = n_span, sk = n_skip;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((tid & 31) == 0 && v) atomicAdd(p.stats + WTHETA_STAT_RECHECK, v);
+        for (int o = 16; o > 0; o >>= 1) {
+            v += __shfl_xor_sync(0xffffffffu, v, o);
+            sp += __shfl_xor_sync(0xffffffffu, sp, o);
+            sk += __shfl_xor_sync(0xffffffffu, sk, o);
+        }
+        if ((tid & 31) == 0) {
+            if (v) atomicAdd(p.stats + WTHETA_STAT_RECHECK, v);
+            if (sp) atomicAdd(p.stats + WTHETA_STAT_SPAN, sp);
+            // pairs of skipped chunks were never computed
+            if (sk) atomicAdd(p.stats + WTHETA_STAT_PAIRS, 0ull - sk);
+        }
         if (tid == 0 && n_items) {
             atomicAdd(p.stats + WTHETA_STAT_TILES, n_items);
             atomicAdd(p.stats + WTHETA_STAT_PAIRS, n_items * (unsigned long long)TA * TB);
@@ -901,51 +1185,62 @@ static int launch_grid(long long n, int sm_count) {
     return (int)std::min<long long>(std::max<long long>(g, 1), (long long)sm_count * 16);
 }
 
-// Cell level of the spatial sort: about 4 or more points per cell on
-// average over the sphere, at most 6 * 4^9 cells.
-static int sort_level(long long n) {
-    int L = 1;
-    while (L < 9 && 6LL * (1LL << (2 * (L + 1))) * 4 <= n) ++L;
-    return L;
+static long long sort_blocks(long long n) {
+    return std::max<long long>(1, (n + kSortTile - 1) / kSortTile);
 }
 
 size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
-    const int L = sort_level(n);
-    const size_t cells = 6ull << (2 * L);
-    size_t b = (size_t)n_pad * 16 + 256;           // FP32 points
-    b += ((size_t)n * 4 + 255) / 256 * 256;        // cell keys
-    b += (cells * 4 + 255) / 256 * 256;            // cell counts
-    if (!is_xyz) b += ((size_t)n * 24 + 255) / 256 * 256;  // FP64 SoA
+    const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
+    size_t b = (size_t)n_pad * 16 + 256;               // FP32 points
+    b += ((size_t)n_pad / 32 * 16 + 255) / 256 * 256;  // chunk bounding spheres
+    b += 4 * a4;                                       // keys and indices, two buffers each
+    b += ((size_t)sort_blocks(n) * 256 * 4 + 255) / 256 * 256;  // digit counts per block
+    if (!is_xyz) b += ((size_t)n * 24 + 255) / 256 * 256;      // FP64 SoA
     return b;
 }
 
 int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int tag,
                    unsigned char* scratch, int sm_count, cudaStream_t st, Prepared* out) {
-    const int L = sort_level(n);
-    const int cells = 6 << (2 * L);
+    const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
+    const long long G = sort_blocks(n);
     unsigned char* sp = scratch;
     float4* p32 = (float4*)sp;
     sp += ((size_t)n_pad * 16 + 255) / 256 * 256;
-    unsigned* key = (unsigned*)sp;
-    sp += ((size_t)n * 4 + 255) / 256 * 256;
-    unsigned* cell = (unsigned*)sp;
-    sp += ((size_t)cells * 4 + 255) / 256 * 256;
+    float4* c32 = (float4*)sp;
+    sp += ((size_t)n_pad / 32 * 16 + 255) / 256 * 256;
+    unsigned* key[2] = {(unsigned*)sp, (unsigned*)(sp + a4)};
+    unsigned* idx[2] = {(unsigned*)(sp + 2 * a4), (unsigned*)(sp + 3 * a4)};
+    sp += 4 * a4;
+    unsigned* hist = (unsigned*)sp;
+    sp += ((size_t)G * 256 * 4 + 255) / 256 * 256;
     const double* x64 = coords;
     long long stride = n;
-    if (!is_xyz) {
+    if (!is_xyz && n > 0) {
         double* x = (double*)sp;
         k_radec_to_xyz<<<launch_grid(n, sm_count), 256, 0, st>>>(coords, n, x, n);
         count_launch();
         x64 = x;
     }
-    int rc = check_cuda(cudaMemsetAsync(cell, 0, (size_t)cells * 4, st));
-    if (rc) return rc;
-    k_cell_count<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, L, is_xyz, key, cell);
-    k_scan_cells<<<1, 1024, 0, st>>>(cell, cells);
-    k_scatter<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(x64, stride, n, n_pad, key, cell, p32,
-                                                            tag);
-    count_launch(3);
+    if (n > 0) {
+        k_sort_keys<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, is_xyz, key[0],
+                                                                idx[0]);
+        count_launch();
+        for (int pass = 0; pass < 4; ++pass) {
+            const int in = pass & 1, o = in ^ 1;
+            k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], n, 8 * pass, hist);
+            k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
+            k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], idx[in], n, 8 * pass,
+                                                                  hist, key[o], idx[o]);
+            count_launch(3);
+        }
+    }
+    // four passes: the order is back in the first buffers
+    k_gather_points<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(x64, stride, n, n_pad, idx[0],
+                                                                  p32, tag);
+    k_chunk_caps<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(p32, n, n_pad, c32);
+    count_launch(2);
     out->p32 = p32;
+    out->c32 = c32;
     out->x64 = x64;
     out->stride = stride;
     return check_cuda(cudaGetLastError());
@@ -964,6 +1259,7 @@ Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long lo
     Segment g;
     std::memset(&g, 0, sizeof(g));
     g.a32 = A.p32; g.b32 = B.p32; g.a64 = A.x64; g.b64 = B.x64;
+    g.b_caps = B.c32;
     g.a64_stride = A.stride; g.b64_stride = B.stride;
     g.tiles_a = ta; g.tiles_b = tb;
     g.item_begin = item_begin;
@@ -989,6 +1285,7 @@ PairParams make_params(const Variant* v, const BinTable& tab, const Segment* seg
                                                             1ull << 30);
     prm.cursor = cursor;
     prm.stats = stats;
+    prm.span = 1;
     std::memcpy(&prm.tab, &tab, sizeof(tab));
     return prm;
 }
@@ -1013,7 +1310,8 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
                  tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
                  tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0 ||
-                 tune->skip_far < 0 || tune->skip_far > 2))
+                 tune->skip_far < 0 || tune->skip_far > 2 || tune->span_bins < 0 ||
+                 tune->span_bins > 2))
         return WTHETA_EINVAL;
     static thread_local BinTable tab;  // large; built per call on the host
     int rc = build_table(edges, K, &tab);
@@ -1094,6 +1392,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
         seg.item_list = list;
         PairParams prm = make_params(v, tab, &seg, nullptr, 0, 0, n_items, cursor, stats);
         prm.n_items_dev = n_list;
+        prm.span = !(tune && tune->span_bins == 2);
         v->kernel<<<grid, v->nt, smem, st>>>(prm);
         count_launch();
         rc = check_cuda(cudaGetLastError());
@@ -1192,7 +1491,7 @@ static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double*
         count_launch();
         return check_cuda(cudaGetLastError());
     }
-    wtheta_tune fixed = {128, 8, 0, 0, 0, 0, 2};  // the tile of WTHETA_NOALLOC_TILE points
+    wtheta_tune fixed = {128, 8, 0, 0, 0, 0, 2, 2};  // the tile of WTHETA_NOALLOC_TILE points
     const Variant* v = pick_variant(&fixed, K, tab.n_lut, di.max_smem_optin);
     if (!v || (long long)v->nt * v->r != T) return WTHETA_EINVAL;
 
@@ -1353,15 +1652,16 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
 
 static int launch_batch_pairs(wtheta_plan* P, const Variant* v, long long item_begin,
                               long long n_items, int grid, size_t smem, cudaStream_t st) {
-    const PairParams prm = make_params(v, P->tab, nullptr, P->d_segs, P->n_segs, item_begin,
-                                       n_items, P->d_cursor, nullptr);
+    PairParams prm = make_params(v, P->tab, nullptr, P->d_segs, P->n_segs, item_begin,
+                                 n_items, P->d_cursor, nullptr);
+    prm.span = P->tune.span_bins != 2;
     v->kernel<<<grid, v->nt, smem, st>>>(prm);
     count_launch();
     return check_cuda(cudaGetLastError());
 }
 
 // Times each candidate shape on the first items of the queue (the biggest
-// counts) and keeps the fastest per item.  Candidates share a tile size per
+// counts) and keeps the fastest per pair.  Candidates share a tile size per
 // layout; a different tile size re-lays the plan out.
 static int autotune(wtheta_plan* P, const DeviceInfo& di, cudaStream_t st, int* best_idx) {
     int nv = 0;
@@ -1396,7 +1696,7 @@ static int autotune(wtheta_plan* P, const DeviceInfo& di, cudaStream_t st, int* 
             if (!rc) rc = check_cuda(cudaEventElapsedTime(&ms, e0, e1));
         }
         if (rc) break;
-        const float per = ms / (float)n_sample;
+        const float per = ms / ((float)n_sample * (float)T * (float)T);  // per pair
         if (per < best) {
             best = per;
             *best_idx = i;
@@ -1527,6 +1827,8 @@ static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, const do
         P->tune.j_per_screen = P->v->ju;
         P->tune.hist_mode = P->v->hm;
         P->tune.deferred = P->v->def + 1;
+        P->tune.skip_far = 2;
+        P->tune.span_bins = tune && tune->span_bins == 2 ? 2 : 1;
         P->smem = P->v->smem(K, P->tab.n_lut);
         rc = plan_layout(P, P->v, di.sm_count, st);
     }

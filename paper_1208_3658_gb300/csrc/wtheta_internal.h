@@ -55,6 +55,7 @@ struct Segment {
     unsigned long long total;    // pairs of the count: n(n-1)/2 or n_a n_b
     long long item_offset;   // item of the count that global item item_begin is
     const unsigned* item_list;   // if set: the count's kept items (tile pairs not skipped)
+    const float4* b_caps;    // bounding spheres of B's chunks of 32 sorted points, or null
     int is_auto;
     int pad_;
 };
@@ -75,6 +76,8 @@ struct PairParams {
     const unsigned long long* n_items_dev;  // if set: at most this many items (device count)
     unsigned long long* cursor;
     unsigned long long* stats;    // WTHETA_NSTATS or null
+    int span;                // settle (A group, B chunk) spans without a lookup per pair
+    int pad_;
     BinTable tab;
 };
 
@@ -94,6 +97,7 @@ struct DeviceInfo {
 // copies padded to whole tiles.
 struct Prepared {
     const float4* p32 = nullptr;
+    const float4* c32 = nullptr;   // bounding sphere of each chunk of 32 sorted points
     const double* x64 = nullptr;
     long long stride = 0;
 };

@@ -78,6 +78,7 @@ struct wtheta_server {
     const Variant* v = nullptr;
     size_t smem = 0;
     int grid = 0;
+    int span = 1;              // settle (A group, B chunk) spans without a lookup per pair
     int sm_count = 0;
     size_t budget = 0;
     size_t resident = 0;
@@ -253,8 +254,9 @@ bool launch_round(wtheta_server* S, Round& R) {
                                         cudaMemcpyHostToDevice, S->comp));
     if (!rc) rc = check_cuda(cudaMemsetAsync(R.d_cursor, 0, 8, S->comp));
     const int grid = (int)std::min<long long>(S->grid, items);
-    const PairParams prm = make_params(S->v, S->tab, nullptr, R.d_segs, n, 0, items, R.d_cursor,
-                                       nullptr);
+    PairParams prm = make_params(S->v, S->tab, nullptr, R.d_segs, n, 0, items, R.d_cursor,
+                                 nullptr);
+    prm.span = S->span;
     if (!rc) rc = launch_pairs(S->v, prm, grid, S->smem, S->comp);
     ++S->kernels;
     // requests whose last tile pairs are in this round: overflow slots, then
@@ -359,6 +361,7 @@ int server_create(const double* edges, int K, size_t budget, int max_active,
         S->max_active = max_active ? max_active : 1024;
         S->sm_count = di.sm_count;
         S->v = pick_variant(tune, K, S->tab.n_lut, di.max_smem_optin);
+        S->span = !(tune && tune->span_bins == 2);
         if (!S->v) rc = WTHETA_EINVAL;
     }
     if (!rc) {

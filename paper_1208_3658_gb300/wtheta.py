@@ -25,7 +25,7 @@ STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: 
 NOALLOC_MAX_POINTS, NOALLOC_TILE = 262144, 1024
 BINS_LINEAR, BINS_LN, BINS_LOG10 = 0, 1, 2
 DERR_NONFINITE, DERR_DEC_RANGE, DERR_NOT_UNIT = 1, 2, 4
-STAT_PAIRS, STAT_RECHECK, STAT_TILES, STAT_SKIPPED, NSTATS = 0, 1, 2, 3, 4
+STAT_PAIRS, STAT_RECHECK, STAT_TILES, STAT_SKIPPED, STAT_SPAN, NSTATS = 0, 1, 2, 3, 4, 5
 
 _lock = threading.Lock()
 _lib = None
@@ -41,7 +41,8 @@ class wtheta_tune(ctypes.Structure):
     _fields_ = [("threads", ctypes.c_int32), ("points_per_thread", ctypes.c_int32),
                 ("hist_mode", ctypes.c_int32), ("j_per_screen", ctypes.c_int32),
                 ("deferred", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
-                ("skip_far", ctypes.c_int32)]
+                ("skip_far", ctypes.c_int32),
+                ("span_bins", ctypes.c_int32)]
 
 
 class wtheta_catalog_pair(ctypes.Structure):
@@ -278,7 +279,7 @@ def _tune_struct(tune):
     return wtheta_tune(int(tune.get("threads", 0)), int(tune.get("points_per_thread", 0)),
                        int(tune.get("hist_mode", 0)), int(tune.get("j_per_screen", 0)),
                        int(tune.get("deferred", 0)), int(tune.get("blocks_per_sm", 0)),
-                       int(tune.get("skip_far", 0)))
+                       int(tune.get("skip_far", 0)), int(tune.get("span_bins", 0)))
 
 
 class BatchPlan:
@@ -328,7 +329,7 @@ def wtheta_batch_info(plan: BatchPlan) -> dict:
     return dict(tune=dict(threads=t.threads, points_per_thread=t.points_per_thread,
                           hist_mode=t.hist_mode, j_per_screen=t.j_per_screen,
                           deferred=t.deferred, blocks_per_sm=t.blocks_per_sm,
-                          skip_far=t.skip_far),
+                          skip_far=t.skip_far, span_bins=t.span_bins),
                 n_items=info.n_items, pairs=info.pairs, evaluated_pairs=info.evaluated_pairs,
                 n_counts=info.n_counts, graph_kernels=info.graph_kernels,
                 autotune_ms=info.autotune_ms, autotuned=bool(info.autotuned))

@@ -318,3 +318,58 @@ def test_skipping_far_tile_pairs_is_exact(W, case):
         assert torch.equal(c_all, c_skip), (case, auto)
         if case != "small":
             assert int(st[W.STAT_SKIPPED]) > 0
+
+
+@pytest.mark.parametrize("case", ["survey_200k", "fullsky_150k", "small", "patch_120k"])
+def test_span_bins_are_exact(W, case):
+    """Settling (A group, B chunk) spans in one slot or with one comparison
+    per pair gives the same counts as binning every pair through the table,
+    and it does settle pairs."""
+    if case == "survey_200k":
+        wl = synth.survey(n=200_000)
+    elif case == "fullsky_150k":
+        wl = synth.largest(n=150_000)
+    elif case == "small":
+        wl = synth.small()
+    else:
+        fp = synth.Patch(200.0, 15.0, 10.0, 25.0)
+        wl = synth.Workload("patch", synth.clustered(fp, 120_000, 2400, 3.0, 5, "test", "data", 0),
+                            synth.uniform(fp, 120_000, 5, "test", "random", 0),
+                            1.0 * ARCMIN, 5.0, 16)
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    d, r = dev(wl.data), dev(wl.rand)
+    for a, b, auto in [(d, None, True), (d, r, False), (r, None, True)]:
+        c_pair = torch.zeros(len(e) + 1, dtype=torch.int64, device="cuda")
+        c_span = torch.zeros_like(c_pair)
+        st = torch.zeros(W.NSTATS, dtype=torch.int64, device="cuda")
+        W.wtheta_count_ex(a, b, False, e, auto, c_pair, tune=dict(span_bins=2))
+        W.wtheta_count_ex(a, b, False, e, auto, c_span, tune=dict(span_bins=1), stats=st)
+        torch.cuda.synchronize()
+        assert torch.equal(c_pair, c_span), (case, auto)
+        st = st.cpu().numpy().astype(np.uint64)
+        assert 0 < st[W.STAT_SPAN] <= st[W.STAT_PAIRS] + st[W.STAT_SPAN], case
+
+
+def test_span_bins_near_an_edge(W):
+    """Two compact clusters whose separation is one bin edge: every chunk span
+    straddles that edge, many pairs fall inside its guard band, and the counts
+    still equal the oracle's bit for bit (P1)."""
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    k = 10
+    rng = np.random.default_rng(17)
+    n = 3000
+    ra = rng.uniform(-0.02, 0.02, n)
+    dec = rng.uniform(-0.02, 0.02, n)
+    A = synth.interleave(ra, dec)
+    B = synth.interleave(ra + e[k], dec)          # the same points, e_k further in RA
+    XA, XB = O.radec_to_xyz(A), O.radec_to_xyz(B)
+    st = torch.zeros(W.NSTATS, dtype=torch.int64, device="cuda")
+    got = gpu_count_xyz(W, XA, XB, e, False, tune=dict(span_bins=1), stats=st)
+    want = O.count_xyz(XA, XB, e, False)
+    assert np.array_equal(got, want)
+    st = st.cpu().numpy()
+    assert st[W.STAT_RECHECK] > 0 and st[W.STAT_SPAN] > 0
+    both = np.concatenate([XA, XB], axis=1)
+    got = gpu_count_xyz(W, both, None, e, True, tune=dict(span_bins=1))
+    want = O.count_xyz(both, None, e, True)
+    assert np.array_equal(got, want)
