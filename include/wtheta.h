@@ -241,7 +241,9 @@ typedef struct wtheta_batch_info_t {
     wtheta_tune tune;          /* the kernel shape in use                    */
     int64_t n_items;           /* tile pairs in the work queue               */
     int64_t pairs;             /* algorithmic pairs of all counts            */
-    int64_t evaluated_pairs;   /* pairs evaluated, tile padding included     */
+    int64_t evaluated_pairs;   /* pairs whose squared chord the last run
+                                  computed (WTHETA_STAT_PAIRS; before the first
+                                  run: all tile pairs); synchronises the device */
     int32_t n_counts;          /* 3 n_cats                                   */
     int32_t graph_kernels;     /* kernel launches per replay                 */
     float autotune_ms;         /* plan-time autotuning cost                  */
@@ -414,6 +416,25 @@ int wtheta_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_
 int wtheta_ls_cross(const uint64_t* D1D2, const uint64_t* D1R2, const uint64_t* R1D2,
                     const uint64_t* R1R2, int64_t n_d1, int64_t n_d2, int64_t n_r1,
                     int64_t n_r2, int32_t n_bins, double* w);
+
+/*
+ * Other estimators over the same counts (the paper leaves the choice of
+ * estimator to the user, Sec. 2), each on counts normalised as in wtheta_ls
+ * (dd, dr, rr), for k = 1..K, in FP64:
+ *   WTHETA_EST_LANDY_SZALAY   ((dd - 2 dr) + rr) / rr      (= wtheta_ls)
+ *   WTHETA_EST_NATURAL        dd / rr - 1                   (Peebles-Hauser)
+ *   WTHETA_EST_DAVIS_PEEBLES  dd / dr - 1
+ *   WTHETA_EST_HAMILTON       (dd rr) / (dr dr) - 1
+ * A bin whose denominator count is 0 gives NaN.  Host arrays of K+2 slots;
+ * w: host, K doubles.  Requires n_d >= 2, n_r >= 2; EINVAL for an unknown
+ * estimator.
+ */
+#define WTHETA_EST_LANDY_SZALAY 0
+#define WTHETA_EST_NATURAL 1
+#define WTHETA_EST_DAVIS_PEEBLES 2
+#define WTHETA_EST_HAMILTON 3
+int wtheta_estimate(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_t n_d,
+                    int64_t n_r, int32_t n_bins, int32_t estimator, double* w);
 
 /*
  * Whole w(theta) from host catalogues: copies data and randoms to the device

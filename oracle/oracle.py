@@ -171,6 +171,31 @@ def ls(DD, DR, RR, n_d: int, n_r: int) -> np.ndarray:
     return w
 
 
+def estimator(DD, DR, RR, n_d: int, n_r: int, name: str) -> np.ndarray:
+    """Other w(theta) estimators over the same counts (Sec. 2 leaves the choice
+    of estimator open), on counts normalised by their pair totals as in Eq. 2:
+    natural (Peebles & Hauser 1974) dd/rr - 1; Davis & Peebles (1983) dd/dr - 1;
+    Hamilton (1993) dd rr / dr^2 - 1; Landy & Szalay (1993) (dd - 2dr + rr)/rr.
+    A bin whose denominator count is 0 gives NaN."""
+    DD, DR, RR = (np.asarray(x, np.uint64)[1:-1].astype(np.float64) for x in (DD, DR, RR))
+    dd = DD / (n_d * (n_d - 1) / 2.0)
+    dr = DR / (float(n_d) * float(n_r))
+    rr = RR / (n_r * (n_r - 1) / 2.0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        if name == "landy_szalay":
+            w = ((dd - 2.0 * dr) + rr) / rr
+            den = RR
+        elif name == "natural":
+            w, den = dd / rr - 1.0, RR
+        elif name == "davis_peebles":
+            w, den = dd / dr - 1.0, DR
+        elif name == "hamilton":
+            w, den = (dd * rr) / (dr * dr) - 1.0, DR
+        else:
+            raise ValueError(name)
+    return np.where(den > 0, w, np.nan)
+
+
 def ls_cross(D1D2, D1R2, R1D2, R1R2, n_d1, n_d2, n_r1, n_r2) -> np.ndarray:
     """Cross-correlation form of Eq. 2 between two catalogues."""
     arrs = [np.ascontiguousarray(x, np.uint64) for x in (D1D2, D1R2, R1D2, R1R2)]

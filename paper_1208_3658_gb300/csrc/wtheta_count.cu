@@ -478,6 +478,18 @@ __global__ void k_chunk_caps(const float4* __restrict__ p32, long long n, long l
     }
 }
 
+// Whether two tiles may hold a pair below the top edge theta_top (radians):
+// their caps' centres are closer than theta_top + both radii (+ 3e-6 rad of
+// slack for the FP64 arithmetic here).  Empty tiles hold no pair.
+__device__ __forceinline__ bool caps_may_meet(const TileCap& A, const TileCap& B,
+                                              double theta_top) {
+    if (!(A.rho >= 0.0 && B.rho >= 0.0)) return false;
+    const double dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
+    const double chord = sqrt(dx * dx + dy * dy + dz * dz);
+    const double theta_c = 2.0 * asin(fmin(1.0, 0.5 * chord));
+    return theta_c - A.rho - B.rho - 3e-6 <= theta_top;
+}
+
 // Keeps the tile pairs that may hold a pair below the top edge: those whose
 // caps are closer than theta_top + margin.  The skipped ones hold only
 // overflow pairs (and empty tiles none), which the overflow slot (total minus
@@ -497,13 +509,7 @@ __global__ void k_cull_items(const TileCap* __restrict__ ca, const TileCap* __re
         if (t < n_items) {
             long long I, J;
             item_to_tiles(t, tiles_a, tiles_b, is_auto, &I, &J);
-            const TileCap A = ca[I], B = cb[J];
-            if (A.rho >= 0.0 && B.rho >= 0.0) {
-                const double dx = A.x - B.x, dy = A.y - B.y, dz = A.z - B.z;
-                const double chord = sqrt(dx * dx + dy * dy + dz * dz);
-                const double theta_c = 2.0 * asin(fmin(1.0, 0.5 * chord));
-                keep = theta_c - A.rho - B.rho - 3e-6 <= theta_top;
-            }
+            keep = caps_may_meet(ca[I], cb[J], theta_top);
             skipped += keep ? 0 : 1;
         }
         const unsigned m = __ballot_sync(0xffffffffu, keep);
@@ -517,6 +523,56 @@ __global__ void k_cull_items(const TileCap* __restrict__ ca, const TileCap* __re
         for (int o = 16; o > 0; o >>= 1) skipped += __shfl_xor_sync(0xffffffffu, skipped, o);
         if (lane == 0 && skipped) atomicAdd(stats + WTHETA_STAT_SKIPPED, skipped);
     }
+}
+
+// The same skipping for a batch's work table.  cs holds every count's items
+// in the full table (begin, n), its tiles' caps and its list; each kept
+// item's index within its count is appended to that count's list (in any
+// order), kept[seg] counting them.
+__global__ void k_cull_batch(const CullSeg* __restrict__ cs, int n_segs, long long total,
+                             double theta_top, unsigned long long* __restrict__ kept) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long n_round = (total + 31) / 32 * 32;
+    const int lane = threadIdx.x & 31;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n_round; g += stride) {
+        bool keep = false;
+        int seg = -1;
+        long long local = 0;
+        if (g < total) {
+            int lo = 0, hi = n_segs - 1;  // last count with begin <= g
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cs[mid].begin <= g) lo = mid; else hi = mid - 1;
+            }
+            seg = lo;
+            local = g - cs[seg].begin;
+            long long I, J;
+            item_to_tiles(local, cs[seg].ta, cs[seg].tb, cs[seg].is_auto, &I, &J);
+            keep = caps_may_meet(cs[seg].ca[I], cs[seg].cb[J], theta_top);
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, keep ? seg : -1);
+        const int leader = __ffs(peers) - 1;
+        unsigned long long base = 0;
+        if (keep && lane == leader) base = atomicAdd(kept + seg, (unsigned long long)__popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (keep) cs[seg].list[base + __popc(peers & ((1u << lane) - 1u))] = (unsigned)local;
+    }
+}
+
+// After k_cull_batch: each count's kept items become a contiguous range of
+// the launch's items, in the table's order; *total receives their number.
+__global__ void k_cull_prefix(Segment* __restrict__ segs, const CullSeg* __restrict__ cs,
+                              const unsigned long long* __restrict__ kept, int n_segs,
+                              unsigned long long* __restrict__ total) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    unsigned long long acc = 0;
+    for (int i = 0; i < n_segs; ++i) {
+        segs[i].item_begin = (long long)acc;
+        segs[i].item_offset = 0;
+        segs[i].item_list = cs[i].list;
+        acc += kept[i];
+    }
+    *total = acc;
 }
 
 // FP64 recheck: the definition's squared chord and slot for the pair of
@@ -944,7 +1000,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
     uint4* sLut = reinterpret_cast<uint4*>(sCap + TB / 32);
     double* sC = reinterpret_cast<double*>(sLut + p.tab.n_lut);
     unsigned* hist = reinterpret_cast<unsigned*>(sC + (K + 2));
-    __shared__ long long s_item;
+    __shared__ long long s_item, s_I, s_J;
 
     const int tid = threadIdx.x;
     const unsigned row_bytes = HCOLS * 4u;
@@ -979,6 +1035,16 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
                 seg = lo;
             }
             s_seg = seg;
+            if (t < n_launch) {
+                // tile pair of the item (one thread: FP64 and 64-bit divisions)
+                const Segment* G = seg < 0 ? &p.seg0 : p.segs + seg;
+                long long local = p.item_begin + t - G->item_begin + G->item_offset;
+                if (G->item_list) local = G->item_list[local];
+                long long I, J;
+                item_to_tiles(local, G->tiles_a, G->tiles_b, G->is_auto, &I, &J);
+                s_I = I;
+                s_J = J;
+            }
         }
         __syncthreads();  // s_item visible; previous item's shared reads finished
         const long long t = s_item;
@@ -995,10 +1061,7 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
             __syncthreads();
         }
         const Segment& S = sSeg;
-        long long I, J;
-        long long local = p.item_begin + t - S.item_begin + S.item_offset;
-        if (S.item_list) local = S.item_list[local];
-        item_to_tiles(local, S.tiles_a, S.tiles_b, S.is_auto, &I, &J);
+        const long long I = s_I, J = s_J;
         const float4* gB = S.b32 + J * TB;
 #pragma unroll 4
         for (int q = 0; q < R; ++q) {
@@ -1425,6 +1488,24 @@ int launch_finalize_segments(const Segment* d_segs, int n_segs, int K, cudaStrea
     return check_cuda(cudaGetLastError());
 }
 
+int launch_tile_caps(const float4* p32, long long n, int T, long long tiles, TileCap* caps,
+                     cudaStream_t st) {
+    if (tiles <= 0) return WTHETA_OK;
+    k_tile_caps<<<(unsigned)tiles, 128, 0, st>>>(p32, n, T, caps);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_cull_items(const TileCap* ca, const TileCap* cb, long long ta, long long tb,
+                      int is_auto, long long n_items, double theta_top, unsigned* list,
+                      unsigned long long* n_list, int sm_count, cudaStream_t st) {
+    if (n_items <= 0) return WTHETA_OK;
+    k_cull_items<<<launch_grid(n_items, sm_count), 256, 0, st>>>(ca, cb, ta, tb, is_auto, n_items,
+                                                                   theta_top, list, n_list, nullptr);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
 void add_launches(long long n) { g_launches.fetch_add((unsigned long long)n); }
 
 // ---------------------------------------------------------------------------
@@ -1559,6 +1640,16 @@ struct wtheta_plan {
     int graph_kernels = 0;
     int grid = 0;
     size_t smem = 0;
+    long long runs = 0;
+    // skipping of far tile pairs, done in the graph on every run
+    int cull = 0;
+    double theta_top = 0.0;
+    void* cull_mem = nullptr;
+    wtheta::CullSeg* d_cull = nullptr;        // per count, in the work table's order
+    unsigned long long* d_kept = nullptr;     // per count
+    unsigned long long* d_total = nullptr;    // kept items of the run
+    unsigned long long* d_stats = nullptr;    // WTHETA_NSTATS of the last run
+    std::vector<wtheta::TileCap*> caps;       // per catalogue
 };
 
 namespace wtheta {
@@ -1619,6 +1710,7 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
     }
     // the work table: DD, DR, RR of every pair, biggest count first
     std::vector<Segment> segs;
+    std::vector<int> seg_cat_a, seg_cat_b;  // prepared catalogue of each side
     P->pairs = 0;
     for (int m = 0; m < nc; ++m) {
         const long long nd = P->cats[m].n_data, nr = P->cats[m].n_rand;
@@ -1633,28 +1725,78 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
                                     c + (P->K + 2), ndr));
         segs.push_back(make_segment(P->prep[2 * m + 1], P->prep[2 * m + 1], tr, tr, 1, 0,
                                     c + 2 * (P->K + 2), nrr));
+        seg_cat_a.insert(seg_cat_a.end(), {2 * m, 2 * m, 2 * m + 1});
+        seg_cat_b.insert(seg_cat_b.end(), {2 * m, 2 * m + 1, 2 * m + 1});
     }
-    std::stable_sort(segs.begin(), segs.end(),
-                     [](const Segment& a, const Segment& b) { return a.n_items > b.n_items; });
+    std::vector<int> order(segs.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return segs[a].n_items > segs[b].n_items; });
+    std::vector<Segment> sorted;
+    std::vector<CullSeg> cull(segs.size());
     long long items = 0;
-    for (auto& g : segs) {
+    for (size_t i = 0; i < order.size(); ++i) {
+        Segment g = segs[order[i]];
         g.item_begin = items;
+        CullSeg& q = cull[i];
+        std::memset(&q, 0, sizeof(q));
+        q.begin = items;
+        q.n = g.n_items;
+        q.ta = g.tiles_a;
+        q.tb = g.tiles_b;
+        q.is_auto = g.is_auto;
         items += g.n_items;
+        sorted.push_back(g);
     }
     P->total_items = items;
-    P->n_segs = (int)segs.size();
+    P->n_segs = (int)sorted.size();
     if (P->d_segs) cudaFree(P->d_segs);
     P->d_segs = nullptr;
-    if ((rc = check_cuda(cudaMalloc(&P->d_segs, sizeof(Segment) * segs.size())))) return rc;
-    return check_cuda(cudaMemcpyAsync(P->d_segs, segs.data(), sizeof(Segment) * segs.size(),
+    if (P->cull_mem) cudaFree(P->cull_mem);
+    P->cull_mem = nullptr;
+    P->caps.assign(2 * nc, nullptr);
+    if ((rc = check_cuda(cudaMalloc(&P->d_segs, sizeof(Segment) * sorted.size())))) return rc;
+    if (P->cull) {
+        // kept counters, total, the count table, every catalogue's tile caps,
+        // and one list of item indices per count
+        size_t cb = ((size_t)P->n_segs * 8 + 8 + 255) / 256 * 256;
+        const size_t off_cs = cb;
+        cb += (sizeof(CullSeg) * P->n_segs + 255) / 256 * 256;
+        std::vector<size_t> off_caps(2 * nc);
+        for (int c = 0; c < 2 * nc; ++c) {
+            off_caps[c] = cb;
+            cb += ((size_t)(P->n_pad[c] / T) * sizeof(TileCap) + 255) / 256 * 256;
+        }
+        const size_t off_lists = cb;
+        cb += (size_t)items * 4;
+        if ((rc = check_cuda(cudaMalloc(&P->cull_mem, cb)))) return rc;
+        unsigned char* cm = (unsigned char*)P->cull_mem;
+        P->d_kept = (unsigned long long*)cm;
+        P->d_total = P->d_kept + P->n_segs;
+        P->d_cull = (CullSeg*)(cm + off_cs);
+        for (int c = 0; c < 2 * nc; ++c) P->caps[c] = (TileCap*)(cm + off_caps[c]);
+        unsigned* lists = (unsigned*)(cm + off_lists);
+        for (size_t i = 0; i < order.size(); ++i) {
+            cull[i].ca = P->caps[seg_cat_a[order[i]]];
+            cull[i].cb = P->caps[seg_cat_b[order[i]]];
+            cull[i].list = lists + cull[i].begin;
+        }
+        rc = check_cuda(cudaMemcpyAsync(P->d_cull, cull.data(), sizeof(CullSeg) * cull.size(),
+                                        cudaMemcpyHostToDevice, st));
+        if (rc) return rc;
+    }
+    return check_cuda(cudaMemcpyAsync(P->d_segs, sorted.data(), sizeof(Segment) * sorted.size(),
                                       cudaMemcpyHostToDevice, st));
 }
 
 static int launch_batch_pairs(wtheta_plan* P, const Variant* v, long long item_begin,
-                              long long n_items, int grid, size_t smem, cudaStream_t st) {
+                              long long n_items, int grid, size_t smem, cudaStream_t st,
+                              const unsigned long long* n_items_dev = nullptr,
+                              unsigned long long* stats = nullptr) {
     PairParams prm = make_params(v, P->tab, nullptr, P->d_segs, P->n_segs, item_begin,
-                                 n_items, P->d_cursor, nullptr);
+                                 n_items, P->d_cursor, stats);
     prm.span = P->tune.span_bins != 2;
+    prm.n_items_dev = n_items_dev;
     v->kernel<<<grid, v->nt, smem, st>>>(prm);
     count_launch();
     return check_cuda(cudaGetLastError());
@@ -1726,10 +1868,31 @@ static int plan_capture(wtheta_plan* P, const DeviceInfo& di) {
                 rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, 1,
                              base + off_b, di.sm_count, cs, &b);
         }
+        if (!rc && P->cull) {
+            // tile caps of every catalogue, the kept tile pairs of every count,
+            // and the launch's item ranges
+            const int T = P->v->nt * P->v->r;
+            for (int c = 0; c < 2 * P->n_cats && !rc; ++c) {
+                const long long n = c % 2 ? P->cats[c / 2].n_rand : P->cats[c / 2].n_data;
+                rc = launch_tile_caps(P->prep[c].p32, n, T, P->n_pad[c] / T, P->caps[c], cs);
+            }
+            if (!rc) rc = check_cuda(cudaMemsetAsync(P->d_kept, 0, (size_t)P->n_segs * 8, cs));
+            if (!rc) {
+                k_cull_batch<<<launch_grid(P->total_items, di.sm_count), 256, 0, cs>>>(
+                    P->d_cull, P->n_segs, P->total_items, P->theta_top, P->d_kept);
+                k_cull_prefix<<<1, 32, 0, cs>>>(P->d_segs, P->d_cull, P->d_kept, P->n_segs,
+                                                P->d_total);
+                count_launch(2);
+                rc = check_cuda(cudaGetLastError());
+            }
+        }
         const size_t nbytes = (size_t)P->n_cats * 3 * (P->K + 2) * sizeof(unsigned long long);
         if (!rc) rc = check_cuda(cudaMemsetAsync(P->d_counts, 0, nbytes, cs));
         if (!rc) rc = check_cuda(cudaMemsetAsync(P->d_cursor, 0, 8, cs));
-        if (!rc) rc = launch_batch_pairs(P, P->v, 0, P->total_items, P->grid, P->smem, cs);
+        if (!rc) rc = check_cuda(cudaMemsetAsync(P->d_stats, 0, 8 * WTHETA_NSTATS, cs));
+        if (!rc)
+            rc = launch_batch_pairs(P, P->v, 0, P->total_items, P->grid, P->smem, cs,
+                                    P->cull ? P->d_total : nullptr, P->d_stats);
         if (!rc) {
             k_finalize_segments<<<(P->n_segs + 127) / 128, 128, 0, cs>>>(P->d_segs, P->n_segs,
                                                                         P->K);
@@ -1759,6 +1922,8 @@ static void plan_release(wtheta_plan* P) {
     if (P->scratch) cudaFree(P->scratch);
     if (P->d_segs) cudaFree(P->d_segs);
     if (P->d_counts) cudaFree(P->d_counts);
+    if (P->cull_mem) cudaFree(P->cull_mem);
+    if (P->d_stats) cudaFree(P->d_stats);
     delete P;
 }
 
@@ -1771,18 +1936,30 @@ static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, const do
     }
     if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
                  tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
-                 tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0))
+                 tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0 ||
+                 tune->skip_far < 0 || tune->skip_far > 2 || tune->span_bins < 0 ||
+                 tune->span_bins > 2))
         return WTHETA_EINVAL;
     wtheta_plan* P = new wtheta_plan();
     P->K = K;
     P->n_cats = n_cats;
     P->cats.assign(cats, cats + n_cats);
     int rc = build_table(edges, K, &P->tab);
+    if (!rc) {
+        P->cull = (!tune || tune->skip_far != 2) && edges[K] < 180.0;
+        P->theta_top = edges[K] * (3.14159265358979323846 / 180.0);
+        // list entries are 32-bit item indices within a count
+        for (int m = 0; m < n_cats; ++m) {
+            const long long t = (std::max(cats[m].n_data, cats[m].n_rand) + 255) / 256;
+            if (t * t >= (1LL << 32)) P->cull = 0;
+        }
+    }
     DeviceInfo di;
     if (!rc) rc = device_info(&di);
     if (!rc) rc = check_cuda(cudaGetDevice(&P->dev));
     if (!rc)
         rc = check_cuda(cudaMalloc(&P->d_counts, (size_t)n_cats * 3 * (K + 2) * sizeof(unsigned long long)));
+    if (!rc) rc = check_cuda(cudaMalloc(&P->d_stats, 8 * WTHETA_NSTATS));
     if (rc) {
         plan_release(P);
         return rc;
@@ -1827,7 +2004,7 @@ static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, const do
         P->tune.j_per_screen = P->v->ju;
         P->tune.hist_mode = P->v->hm;
         P->tune.deferred = P->v->def + 1;
-        P->tune.skip_far = 2;
+        P->tune.skip_far = P->cull ? 1 : 2;
         P->tune.span_bins = tune && tune->span_bins == 2 ? 2 : 1;
         P->smem = P->v->smem(K, P->tab.n_lut);
         rc = plan_layout(P, P->v, di.sm_count, st);
@@ -1905,6 +2082,7 @@ int wtheta_batch_run(wtheta_plan* P, uint64_t* counts, void* stream) {
     int rc = check_cuda(cudaGraphLaunch(P->exec, st));
     if (rc) return rc;
     count_launch((unsigned)P->graph_kernels);
+    ++P->runs;
     const size_t bytes = (size_t)P->n_cats * 3 * (P->K + 2) * sizeof(unsigned long long);
     return check_cuda(cudaMemcpyAsync(counts, P->d_counts, bytes, cudaMemcpyDeviceToDevice, st));
 }
@@ -1917,6 +2095,14 @@ int wtheta_batch_info(const wtheta_plan* P, wtheta_batch_info_t* info) {
     info->pairs = P->pairs;
     const long long T = (long long)P->v->nt * P->v->r;
     info->evaluated_pairs = P->total_items * T * T;
+    if (P->runs > 0) {
+        // pairs whose squared chord the last run computed (it must have finished)
+        unsigned long long st[WTHETA_NSTATS];
+        if (cudaDeviceSynchronize() != cudaSuccess ||
+            cudaMemcpy(st, P->d_stats, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return WTHETA_ECUDA;
+        info->evaluated_pairs = (long long)st[WTHETA_STAT_PAIRS];
+    }
     info->n_counts = 3 * P->n_cats;
     info->graph_kernels = P->graph_kernels;
     info->autotune_ms = P->autotune_ms;

@@ -2,6 +2,7 @@
 // (App. A geometry), the FP32 guard band and screening table used by the
 // counting kernels, and the Landy-Szalay estimator (Eq. 2).
 #include <cmath>
+#include <limits>
 #include <cstring>
 
 #include "wtheta_internal.h"
@@ -287,6 +288,29 @@ int wtheta_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_
         const double dr = (double)DR[k] / Ndr;
         const double rr = (double)RR[k] / Nrr;
         w[k - 1] = ((dd - 2.0 * dr) + rr) / rr;
+    }
+    return WTHETA_OK;
+}
+
+int wtheta_estimate(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_t nd,
+                    int64_t nr, int32_t K, int32_t est, double* w) {
+    if (!DD || !DR || !RR || !w || K < 1 || K > kMaxBins || nd < 2 || nr < 2 || est < 0 ||
+        est > WTHETA_EST_HAMILTON)
+        return WTHETA_EINVAL;
+    if (est == WTHETA_EST_LANDY_SZALAY) return wtheta_ls(DD, DR, RR, nd, nr, K, w);
+    const double Ndd = (double)nd * (double)(nd - 1) / 2.0;
+    const double Ndr = (double)nd * (double)nr;
+    const double Nrr = (double)nr * (double)(nr - 1) / 2.0;
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    for (int k = 1; k <= K; ++k) {
+        const double dd = (double)DD[k] / Ndd;
+        const double dr = (double)DR[k] / Ndr;
+        const double rr = (double)RR[k] / Nrr;
+        double v;
+        if (est == WTHETA_EST_NATURAL) v = RR[k] ? dd / rr - 1.0 : nan;
+        else if (est == WTHETA_EST_DAVIS_PEEBLES) v = DR[k] ? dd / dr - 1.0 : nan;
+        else v = DR[k] ? (dd * rr) / (dr * dr) - 1.0 : nan;
+        w[k - 1] = v;
     }
     return WTHETA_OK;
 }

@@ -66,6 +66,18 @@ struct TileCap {
     double x, y, z, rho;     // rho < 0: no real point in the tile
 };
 
+// One count of a batch, for skipping its far tile pairs on the device: its
+// items in the full work table, its tiles' caps, and the list of kept items.
+struct CullSeg {
+    long long begin, n;
+    const TileCap* ca;
+    const TileCap* cb;
+    long long ta, tb;
+    unsigned* list;
+    int is_auto;
+    int pad_;
+};
+
 struct PairParams {
     Segment seg0;            // the count, when n_segs == 0
     const Segment* segs;     // device table sorted by item_begin, when n_segs > 0
@@ -123,6 +135,14 @@ PairParams make_params(const Variant* v, const BinTable& tab, const Segment* seg
                        unsigned long long* cursor, unsigned long long* stats);
 int launch_pairs(const Variant* v, const PairParams& prm, int grid, size_t smem, cudaStream_t st);
 int launch_finalize_segments(const Segment* d_segs, int n_segs, int K, cudaStream_t st);
+// Bounding cap of every tile of T points (real points [0, n)).
+int launch_tile_caps(const float4* p32, long long n, int T, long long tiles, TileCap* caps,
+                     cudaStream_t st);
+// Appends the items of one count that caps_may_meet keeps (indices < 2^32)
+// to list, counting them in *n_list (which the caller zeroes).
+int launch_cull_items(const TileCap* ca, const TileCap* cb, long long ta, long long tb,
+                      int is_auto, long long n_items, double theta_top, unsigned* list,
+                      unsigned long long* n_list, int sm_count, cudaStream_t st);
 void add_launches(long long n);
 
 // Host-side helpers (wtheta_host.cpp).

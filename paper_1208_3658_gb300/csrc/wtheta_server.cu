@@ -6,9 +6,12 @@
 //   - admission: requests wait in arrival order until their device copies fit
 //     under the memory budget; an admitted request is uploaded and put in
 //     spatial order on an upload stream, overlapping the counting;
+//   - skipping: once a request is in spatial order, the tile pairs of its
+//     counts that lie wholly beyond the top edge are dropped (their pairs are
+//     overflow), so rounds carry only tile pairs that can land in a bin;
 //   - rounds: one persistent pair-count launch over a segment table drawn from
-//     every admitted, ready request (the oldest gets up to half of the round's
-//     tile pairs, the rest is shared fairly); a request that arrives while
+//     every admitted, ready request: small requests first (up to half of a
+//     round), then the others in arrival order; a request that arrives while
 //     others are counting joins the next round instead of queueing behind them;
 //   - completion: after the round that holds a request's last tile pairs, the
 //     overflow slots and the copy of its counts to the host are queued on the
@@ -51,13 +54,16 @@ struct Request {
     Segment* d_segs = nullptr;                   // the request's counts, for finalize
     Segment seg[4];                              // templates (item_offset = 0)
     long long sched[4] = {0, 0, 0, 0};           // tile pairs handed to rounds so far
-    unsigned long long* host_counts = nullptr;   // pinned, ncount x (K+2)
+    unsigned long long* host_counts = nullptr;   // pinned, ncount x (K+2), then 4 kept counts
+    unsigned long long* d_kept = nullptr;        // tile pairs kept per count (far ones skipped)
+    unsigned* d_list[4] = {nullptr, nullptr, nullptr, nullptr};  // kept items per count
     cudaEvent_t ready = nullptr, finished = nullptr;
     int state = kQueued;
     int status = WTHETA_OK;
     double t_submit = 0, t_admit = 0, t_done = 0;
     std::vector<double> w;
     long long pairs = 0;
+    int cull = 0;                                // far tile pairs skipped
 };
 
 struct Round {
@@ -79,6 +85,8 @@ struct wtheta_server {
     size_t smem = 0;
     int grid = 0;
     int span = 1;              // settle (A group, B chunk) spans without a lookup per pair
+    int cull = 1;              // skip tile pairs wholly beyond the top edge
+    double theta_top = 0.0;    // top edge, radians
     int sm_count = 0;
     size_t budget = 0;
     size_t resident = 0;
@@ -106,6 +114,26 @@ double now_s(const wtheta_server* S) {
     return std::chrono::duration<double>(Clock::now() - S->t0).count();
 }
 
+// Tile pairs of count k of a request (catalogue pairs as in admit).
+long long count_items(const Request* r, long long T, int k) {
+    static const int auto_a[3] = {0, 0, 1}, auto_b[3] = {0, 1, 1};
+    static const int cross_a[4] = {0, 0, 1, 1}, cross_b[4] = {2, 3, 2, 3};
+    const bool aut = r->kind == WTHETA_REQ_AUTO;
+    const long long ta = round_up(r->n[aut ? auto_a[k] : cross_a[k]], T) / T;
+    const long long tb = round_up(r->n[aut ? auto_b[k] : cross_b[k]], T) / T;
+    return aut && auto_a[k] == auto_b[k] ? ta * (ta + 1) / 2 : ta * tb;
+}
+
+size_t cull_bytes(const wtheta_server* S, const Request* r) {
+    if (!r->cull) return 0;
+    const long long T = (long long)S->v->nt * S->v->r;
+    size_t b = 256;                                    // kept counters
+    for (int c = 0; c < r->ncat; ++c)
+        b += ((size_t)(round_up(r->n[c], T) / T) * sizeof(TileCap) + 255) / 256 * 256;
+    for (int k = 0; k < r->ncount; ++k) b += ((size_t)count_items(r, T, k) * 4 + 255) / 256 * 256;
+    return b;
+}
+
 size_t request_bytes(const wtheta_server* S, const Request* r) {
     const long long T = (long long)S->v->nt * S->v->r;
     size_t b = 0;
@@ -113,6 +141,7 @@ size_t request_bytes(const wtheta_server* S, const Request* r) {
         b += (prepare_bytes(r->n[c], round_up(r->n[c], T), 0) + 255) / 256 * 256;
     b += (size_t)r->ncount * (S->K + 2) * 8 + 256;    // counts
     b += sizeof(Segment) * 4 + 256;                    // the request's segment table
+    b += cull_bytes(S, r);                             // caps and kept tile pairs
     return b;
 }
 
@@ -181,8 +210,48 @@ int admit(wtheta_server* S, Request* r) {
     for (int k = 0; k < r->ncount; ++k) r->pairs += (long long)r->seg[k].total;
     rc = check_cuda(cudaMemcpyAsync(r->d_segs, r->seg, sizeof(Segment) * r->ncount,
                                     cudaMemcpyHostToDevice, S->up));
+    if (!rc && r->cull) {
+        // bounding caps of every catalogue's tiles, then each count's tile
+        // pairs that may hold a pair below the top edge; the kept numbers come
+        // back to the host before the request is ready
+        r->d_kept = (unsigned long long*)p;
+        p += 256;
+        TileCap* caps[4] = {nullptr, nullptr, nullptr, nullptr};
+        for (int c = 0; c < r->ncat && !rc; ++c) {
+            caps[c] = (TileCap*)p;
+            const long long tiles = round_up(r->n[c], T) / T;
+            p += ((size_t)tiles * sizeof(TileCap) + 255) / 256 * 256;
+            rc = launch_tile_caps(r->prep[c].p32, r->n[c], (int)T, tiles, caps[c], S->up);
+        }
+        if (!rc) rc = check_cuda(cudaMemsetAsync(r->d_kept, 0, 4 * 8, S->up));
+        static const int auto_a[3] = {0, 0, 1}, auto_b[3] = {0, 1, 1};
+        static const int cross_a[4] = {0, 0, 1, 1}, cross_b[4] = {2, 3, 2, 3};
+        const bool aut = r->kind == WTHETA_REQ_AUTO;
+        for (int k = 0; k < r->ncount && !rc; ++k) {
+            r->d_list[k] = (unsigned*)p;
+            p += ((size_t)r->seg[k].n_items * 4 + 255) / 256 * 256;
+            const int a = aut ? auto_a[k] : cross_a[k], b = aut ? auto_b[k] : cross_b[k];
+            rc = launch_cull_items(caps[a], caps[b], r->seg[k].tiles_a, r->seg[k].tiles_b,
+                                   r->seg[k].is_auto, r->seg[k].n_items, S->theta_top,
+                                   r->d_list[k], r->d_kept + k, S->sm_count, S->up);
+        }
+        if (!rc)
+            rc = check_cuda(cudaMemcpyAsync(r->host_counts + (size_t)r->ncount * K2, r->d_kept,
+                                            (size_t)r->ncount * 8, cudaMemcpyDeviceToHost, S->up));
+    }
     if (!rc) rc = check_cuda(cudaEventRecord(r->ready, S->up));
     return rc;
+}
+
+// The request's uploads, ordering and skipping have finished: its counts
+// take only the kept tile pairs.
+void on_ready(const wtheta_server* S, Request* r) {
+    if (!r->cull) return;
+    const unsigned long long* kept = r->host_counts + (size_t)r->ncount * (S->K + 2);
+    for (int k = 0; k < r->ncount; ++k) {
+        r->seg[k].n_items = (long long)kept[k];
+        r->seg[k].item_list = r->d_list[k];
+    }
 }
 
 long long remaining(const Request* r) {
@@ -196,34 +265,34 @@ long long remaining(const Request* r) {
 bool launch_round(wtheta_server* S, Round& R) {
     std::vector<Request*> ready;
     for (Request* r : S->active)
-        if (r->state == kCounting && remaining(r) > 0) ready.push_back(r);
-        else if (r->state == kUploading && cudaEventQuery(r->ready) == cudaSuccess) {
+        if (r->state == kCounting && remaining(r) > 0) {
+            ready.push_back(r);
+        } else if (r->state == kUploading && cudaEventQuery(r->ready) == cudaSuccess) {
             r->state = kCounting;
-            if (remaining(r) > 0) ready.push_back(r);
+            on_ready(S, r);
+            ready.push_back(r);  // even with no tile pair left: it still has to finish
         }
     if (ready.empty()) return false;
-    // the oldest request takes up to half of the round (so a large request
-    // that has waited longest keeps moving), the rest is shared fairly, and
-    // leftovers go to whoever still has work
+    // Small requests (all their remaining tile pairs fit in an eighth of a
+    // round) go first, up to half of the round, so that they are not held
+    // behind large ones; the rest of the round goes to the others in arrival
+    // order, each taking what it needs, so that a large request is delayed
+    // only by earlier ones and by small ones.
     long long budget = S->round_items;
+    const long long small_items = S->round_items / 8;
+    long long small_budget = budget / 2;
     std::vector<long long> give(ready.size(), 0);
-    give[0] = std::min(remaining(ready[0]), budget / 2);
-    budget -= give[0];
-    while (budget > 0) {
-        long long want = 0;
-        for (size_t i = 0; i < ready.size(); ++i) want += remaining(ready[i]) - give[i] > 0;
-        if (!want) break;
-        const long long share = std::max<long long>(1, budget / want);
-        bool any = false;
-        for (size_t i = 0; i < ready.size() && budget > 0; ++i) {
-            const long long left = remaining(ready[i]) - give[i];
-            if (left <= 0) continue;
-            const long long g = std::min(left, std::min(share, budget));
-            give[i] += g;
-            budget -= g;
-            any = true;
-        }
-        if (!any) break;
+    for (size_t i = 0; i < ready.size() && small_budget > 0; ++i) {
+        const long long rem = remaining(ready[i]);
+        if (rem > small_items) continue;
+        give[i] = std::min(rem, small_budget);
+        small_budget -= give[i];
+        budget -= give[i];
+    }
+    for (size_t i = 0; i < ready.size() && budget > 0; ++i) {
+        const long long g = std::min(remaining(ready[i]) - give[i], budget);
+        give[i] += g;
+        budget -= g;
     }
     // segment table of the round
     int n = 0;
@@ -247,18 +316,21 @@ bool launch_round(wtheta_server* S, Round& R) {
         }
         if (remaining(r) == 0) finishing.push_back(r);
     }
-    if (n == 0) return false;
+    if (n == 0 && finishing.empty()) return false;
     // every request in the round must be ready on the compute stream
     for (Request* r : ready) cudaStreamWaitEvent(S->comp, r->ready, 0);
-    int rc = check_cuda(cudaMemcpyAsync(R.d_segs, R.h_segs, sizeof(Segment) * n,
+    int rc = WTHETA_OK;
+    if (n > 0) {
+        rc = check_cuda(cudaMemcpyAsync(R.d_segs, R.h_segs, sizeof(Segment) * n,
                                         cudaMemcpyHostToDevice, S->comp));
-    if (!rc) rc = check_cuda(cudaMemsetAsync(R.d_cursor, 0, 8, S->comp));
-    const int grid = (int)std::min<long long>(S->grid, items);
-    PairParams prm = make_params(S->v, S->tab, nullptr, R.d_segs, n, 0, items, R.d_cursor,
-                                 nullptr);
-    prm.span = S->span;
-    if (!rc) rc = launch_pairs(S->v, prm, grid, S->smem, S->comp);
-    ++S->kernels;
+        if (!rc) rc = check_cuda(cudaMemsetAsync(R.d_cursor, 0, 8, S->comp));
+        const int grid = (int)std::min<long long>(S->grid, items);
+        PairParams prm = make_params(S->v, S->tab, nullptr, R.d_segs, n, 0, items, R.d_cursor,
+                                     nullptr);
+        prm.span = S->span;
+        if (!rc) rc = launch_pairs(S->v, prm, grid, S->smem, S->comp);
+        ++S->kernels;
+    }
     // requests whose last tile pairs are in this round: overflow slots, then
     // their counts to the host, in stream order after the round
     for (Request* r : finishing) {
@@ -362,6 +434,8 @@ int server_create(const double* edges, int K, size_t budget, int max_active,
         S->sm_count = di.sm_count;
         S->v = pick_variant(tune, K, S->tab.n_lut, di.max_smem_optin);
         S->span = !(tune && tune->span_bins == 2);
+        S->cull = !(tune && tune->skip_far == 2) && edges[K] < 180.0;
+        S->theta_top = edges[K] * (3.14159265358979323846 / 180.0);
         if (!S->v) rc = WTHETA_EINVAL;
     }
     if (!rc) {
@@ -415,6 +489,12 @@ int wtheta_server_submit(wtheta_server* S, const wtheta_request* q, uint64_t* re
         if (!src[c] || n[c] < 2) rc = WTHETA_EINVAL;
     if (!rc) {
         for (int c = 0; c < r->ncat; ++c) r->n[c] = n[c];
+        // far tile pairs are skipped unless a count has 2^32 tile pairs or more
+        // (kept items are listed by 32-bit index)
+        const long long T = (long long)S->v->nt * S->v->r;
+        r->cull = S->cull;
+        for (int k = 0; k < r->ncount; ++k)
+            if (count_items(r, T, k) >= (1LL << 32)) r->cull = 0;
         r->dev_bytes = request_bytes(S, r);
         if (r->dev_bytes > S->budget) rc = WTHETA_EBUDGET;
     }
@@ -423,7 +503,7 @@ int wtheta_server_submit(wtheta_server* S, const wtheta_request* q, uint64_t* re
         rc = check_cuda(cudaMallocHost(&r->host_in[c], (size_t)n[c] * 16));
         if (!rc) std::memcpy(r->host_in[c], src[c], (size_t)n[c] * 16);
     }
-    if (!rc) rc = check_cuda(cudaMallocHost(&r->host_counts, (size_t)r->ncount * (S->K + 2) * 8));
+    if (!rc) rc = check_cuda(cudaMallocHost(&r->host_counts, ((size_t)r->ncount * (S->K + 2) + 4) * 8));
     if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming));
     if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&r->finished, cudaEventDisableTiming));
     if (rc) {

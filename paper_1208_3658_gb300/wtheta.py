@@ -58,6 +58,7 @@ class wtheta_batch_info_t(ctypes.Structure):
 
 
 REQ_AUTO, REQ_CROSS = 0, 1
+EST_LANDY_SZALAY, EST_NATURAL, EST_DAVIS_PEEBLES, EST_HAMILTON = 0, 1, 2, 3
 RS_QUEUED, RS_UPLOADING, RS_COUNTING, RS_FINISHING, RS_DONE, RS_FAILED = range(6)
 
 
@@ -112,6 +113,7 @@ def lib() -> ctypes.CDLL:
             L.wtheta_get_error.argtypes = [vp, u32p]
             L.wtheta_ls.argtypes = [u64p, u64p, u64p, i64, i64, i32, dp]
             L.wtheta_ls_cross.argtypes = [u64p, u64p, u64p, u64p, i64, i64, i64, i64, i32, dp]
+            L.wtheta_estimate.argtypes = [u64p, u64p, u64p, i64, i64, i32, i32, dp]
             L.wtheta_correlate.argtypes = [dp, i64, dp, i64, dp, i32, u64p, dp, vp]
             L.wtheta_count_xyz_noalloc.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
             L.wtheta_batch_plan.argtypes = [ctypes.POINTER(wtheta_catalog_pair), i32, dp, i32,
@@ -463,6 +465,15 @@ def wtheta_ls(DD, DR, RR, n_d: int, n_r: int) -> np.ndarray:
     K = len(DD) - 2
     w = np.empty(K, np.float64)
     _check(lib().wtheta_ls(p1, p2, p3, n_d, n_r, K, _host_f64(w)[1]), "wtheta_ls")
+    return w
+
+
+def wtheta_estimate(DD, DR, RR, n_d: int, n_r: int, estimator: int) -> np.ndarray:
+    (DD, p1), (DR, p2), (RR, p3) = _host_u64(DD), _host_u64(DR), _host_u64(RR)
+    K = len(DD) - 2
+    w = np.empty(K, np.float64)
+    _check(lib().wtheta_estimate(p1, p2, p3, n_d, n_r, K, estimator, _host_f64(w)[1]),
+           "wtheta_estimate")
     return w
 
 

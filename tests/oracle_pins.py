@@ -125,6 +125,38 @@ def check_r_is_d_twice():
     assert np.all(np.abs(w[nz] - want) <= 1e-12 * 3.0), (w[nz], want)
 
 
+def check_estimators_closed_forms():
+    """The other estimators on the two closed-form cases above.  R = D
+    (n_r = n): dd = rr = 2P/(n(n-1)), dr = 2P/n^2, so natural = 0,
+    Davis-Peebles = n/(n-1) - 1 = 1/(n-1), Hamilton = n^2/(n-1)^2 - 1 =
+    (2n-1)/(n-1)^2.  R = D twice (n_r = 2n): dd = 2P/(n(n-1)), dr = 2P/n^2,
+    rr = 4P/(n(2n-1)), so natural = 1/(2(n-1)), Davis-Peebles = 1/(n-1),
+    Hamilton = 2n^2/((n-1)(2n-1)) - 1 = (3n-1)/((n-1)(2n-1))."""
+    e = O.edges(1.0 * ARCMIN, 5.0, 16)
+    n = 700
+    D = _clustered(n, 9)
+    DD = O.count(D, None, e, True)
+    DR = O.count(D, D, e, False)
+    nz = DD[1:-1] > 0
+    assert nz.sum() >= 10
+    for name, want in [("natural", 0.0), ("davis_peebles", 1.0 / (n - 1)),
+                       ("hamilton", (2 * n - 1) / (n - 1) ** 2),
+                       ("landy_szalay", 2.0 / n)]:
+        w = O.estimator(DD, DR, DD, n, n, name)
+        assert np.all(np.abs(w[nz] - want) <= 1e-12 * max(abs(want), 1e-3)), (name, w[nz], want)
+    R = np.concatenate([D, D])
+    DR2 = O.count(D, R, e, False)
+    RR2 = O.count(R, None, e, True)
+    for name, want in [("natural", 1.0 / (2 * (n - 1))), ("davis_peebles", 1.0 / (n - 1)),
+                       ("hamilton", (3 * n - 1) / ((n - 1) * (2 * n - 1))),
+                       ("landy_szalay", (3 * n - 2) / (2 * n * (n - 1)))]:
+        w = O.estimator(DD, DR2, RR2, n, 2 * n, name)
+        assert np.all(np.abs(w[nz] - want) <= 1e-12 * abs(want)), (name, w[nz], want)
+    # empty bins of the denominator give NaN
+    z = np.zeros(18, np.uint64)
+    assert np.all(np.isnan(O.estimator(z, z, z, 10, 10, "hamilton")))
+
+
 def check_cross_identity():
     """Cross estimator with R1 = D1: d1d2 - d1r2 - r1d2 + r1r2 = 0."""
     e = O.edges(1.0 * ARCMIN, 5.0, 16)
@@ -203,6 +235,6 @@ def check_chord_values():
 
 ALL_CHECKS = [
     check_hand_placed, check_totals, check_dr_rd, check_d_equals_r,
-    check_r_is_d_twice, check_cross_identity, check_analytic_rr,
+    check_r_is_d_twice, check_estimators_closed_forms, check_cross_identity, check_analytic_rr,
     check_bruteforce_angles, check_edges_modes, check_chord_values,
 ]

@@ -211,3 +211,24 @@ def test_server_validation_needs_no_gpu():
     assert L.wtheta_server_destroy(None) == -1
     d = ctypes.c_int32()
     assert L.wtheta_server_wait(None, 1, 0, ctypes.byref(d), None, None) == -1
+
+
+@pytest.mark.parametrize("est,name", [(W.EST_LANDY_SZALAY, "landy_szalay"),
+                                      (W.EST_NATURAL, "natural"),
+                                      (W.EST_DAVIS_PEEBLES, "davis_peebles"),
+                                      (W.EST_HAMILTON, "hamilton")])
+def test_estimators_match_oracle(est, name):
+    wl = synth.small(n=1200)
+    e = O.edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    DD, DR, RR, _ = O.wtheta(wl.data, wl.rand, e)
+    DR = DR.copy()
+    DR[3] = 0                      # an empty denominator bin for two of them
+    got = W.wtheta_estimate(DD, DR, RR, wl.n_d, wl.n_r, est)
+    want = O.estimator(DD, DR, RR, wl.n_d, wl.n_r, name)
+    assert np.array_equal(np.isnan(got), np.isnan(want))
+    ok = ~np.isnan(want)
+    assert np.all(np.abs(got[ok] - want[ok]) <= 1e-13 * np.maximum(np.abs(want[ok]), 1.0))
+    if est == W.EST_LANDY_SZALAY:
+        assert np.array_equal(got, W.wtheta_ls(DD, DR, RR, wl.n_d, wl.n_r), equal_nan=True)
+    with pytest.raises(W.WthetaError):
+        W.wtheta_estimate(DD, DR, RR, wl.n_d, wl.n_r, 4)
