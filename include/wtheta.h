@@ -60,6 +60,7 @@ extern "C" {
 #define WTHETA_DERR_NONFINITE 1u  /* an input coordinate is NaN or infinite  */
 #define WTHETA_DERR_DEC_RANGE 2u  /* |Dec| > 90 degrees                      */
 #define WTHETA_DERR_NOT_UNIT 4u   /* an xyz input is not a unit vector       */
+#define WTHETA_DERR_LABEL 8u      /* a region label outside [0, n_regions)  */
 
 /* ---- binning modes (Sec. 2.1: evenly spaced, natural-log, base-10 log) -- */
 #define WTHETA_BINS_LINEAR 0
@@ -435,6 +436,42 @@ int wtheta_ls_cross(const uint64_t* D1D2, const uint64_t* D1R2, const uint64_t* 
 #define WTHETA_EST_HAMILTON 3
 int wtheta_estimate(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_t n_d,
                     int64_t n_r, int32_t n_bins, int32_t estimator, double* w);
+
+/*
+ * Jackknife regions.  Sec. 4 of the paper points at error estimates of
+ * w(theta) from many realisations; the delete-one jackknife draws them from
+ * the survey itself, cut into R regions.  wtheta_count_regions counts DD, DR
+ * and RR split by region pair, in one persistent launch:
+ *   coords_d, coords_r: device, as wtheta_count_ex (RA/Dec degrees, or SoA
+ *     unit vectors when coords_are_xyz = 1);
+ *   labels_d, labels_r: device int32, the region of every point, in
+ *     [0, n_regions); 1 <= n_regions <= 256 (a label outside sets
+ *     WTHETA_DERR_LABEL in the device error word and counts as region 0);
+ *   counts: device, 3 x R x R x (K+2) uint64, laid out [DD, DR, RR][a][b][slot]:
+ *     DD and RR hold the pairs with one point in region a and the other in
+ *     region b for a <= b (a = b: both in a) and zeros for a > b; DR holds
+ *     the pairs of a data point in region a and a random point in region b;
+ *   region_sizes: host, 2 x R int64 (points per region: data, then randoms).
+ * Synchronises stream once (the region sizes decide the launch's layout).
+ * Summing the region pairs gives wtheta_count's DD, DR and RR.
+ */
+int wtheta_count_regions(const double* coords_d, int64_t n_d, const int32_t* labels_d,
+                         const double* coords_r, int64_t n_r, const int32_t* labels_r,
+                         int32_t coords_are_xyz, const double* bin_edges_deg, int32_t n_bins,
+                         int32_t n_regions, uint64_t* counts, int64_t* region_sizes,
+                         void* stream);
+
+/*
+ * Delete-one jackknife of the Landy-Szalay w(theta) from region-pair counts
+ * (host copies of wtheta_count_regions' outputs).  Sample k drops every pair
+ * with a point in region k and the region's points from the pair totals:
+ *   w: K doubles, the estimate from all regions (= wtheta_ls of the sums);
+ *   w_jk: R x K doubles, sample k in row k;
+ *   cov: K x K doubles, (R-1)/R sum_k (w_k - mean)(w_k - mean)^T.
+ * Requires 2 <= R <= 256.
+ */
+int wtheta_jackknife(const uint64_t* counts, const int64_t* region_sizes, int32_t n_regions,
+                     int32_t n_bins, double* w, double* w_jk, double* cov);
 
 /*
  * Whole w(theta) from host catalogues: copies data and randoms to the device

@@ -196,6 +196,52 @@ def estimator(DD, DR, RR, n_d: int, n_r: int, name: str) -> np.ndarray:
     return np.where(den > 0, w, np.nan)
 
 
+def count_regions(xyz_d, labels_d, xyz_r, labels_r, edges_deg, n_regions: int) -> np.ndarray:
+    """DD, DR, RR split by region pair, by the definition: the pairs of Sec. 2
+    with one point in region a and the other in region b.  Layout
+    [DD, DR, RR][a][b][slot]; DD and RR fill a <= b only (a = b: both points
+    in a), DR every (a, b) with the data point in a."""
+    K = len(edges_deg) - 1
+    R = n_regions
+    out = np.zeros((3, R, R, K + 2), np.uint64)
+    D = [np.ascontiguousarray(xyz_d[:, labels_d == a]) for a in range(R)]
+    Q = [np.ascontiguousarray(xyz_r[:, labels_r == a]) for a in range(R)]
+    for a in range(R):
+        for b in range(R):
+            out[1, a, b] = count_xyz(D[a], Q[b], edges_deg, False)
+            if b < a:
+                continue
+            for kind, S in ((0, D), (2, Q)):
+                if a == b:
+                    out[kind, a, a] = count_xyz(S[a], None, edges_deg, True)
+                else:
+                    out[kind, a, b] = count_xyz(S[a], S[b], edges_deg, False)
+    return out
+
+
+def jackknife(region_counts: np.ndarray, sizes: np.ndarray, n_regions: int):
+    """Delete-one jackknife of Eq. 2 (the error estimate Sec. 4 points at):
+    sample k keeps the region pairs (a, b) with a != k and b != k and the
+    points outside region k; returns w (all regions), w_k (R x K) and
+    cov = (R-1)/R sum_k (w_k - mean)(w_k - mean)^T."""
+    R = n_regions
+    c = np.asarray(region_counts, np.uint64)
+    nd, nr = np.asarray(sizes[:R], np.int64), np.asarray(sizes[R:], np.int64)
+    full = [c[kind].sum(axis=(0, 1), dtype=np.uint64) for kind in range(3)]
+    w = ls(full[0], full[1], full[2], int(nd.sum()), int(nr.sum()))
+    K = len(w)
+    w_k = np.empty((R, K))
+    for k in range(R):
+        keep = np.ones(R, bool)
+        keep[k] = False
+        s = [c[kind][np.ix_(keep, keep)].sum(axis=(0, 1), dtype=np.uint64) for kind in range(3)]
+        w_k[k] = ls(s[0], s[1], s[2], int(nd.sum() - nd[k]), int(nr.sum() - nr[k]))
+    mean = w_k.mean(axis=0)
+    dev = w_k - mean
+    cov = (R - 1) / R * (dev.T @ dev)
+    return w, w_k, cov
+
+
 def ls_cross(D1D2, D1R2, R1D2, R1R2, n_d1, n_d2, n_r1, n_r2) -> np.ndarray:
     """Cross-correlation form of Eq. 2 between two catalogues."""
     arrs = [np.ascontiguousarray(x, np.uint64) for x in (D1D2, D1R2, R1D2, R1R2)]

@@ -53,6 +53,8 @@ static inline void count_launch(unsigned n = 1) { g_launches.fetch_add(n, std::m
 
 static constexpr float kSentinel = 1.0e10f;  // sentinel offset; (1e10)^2 >> 4
 
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
 __device__ __forceinline__ float min3f(float a, float b, float c) {
     float d;
     asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -351,6 +353,60 @@ __global__ void k_gather_points(const double* __restrict__ xyz, long long stride
     }
 }
 
+// Labels in sorted order (the digit of one more radix pass); a label outside
+// [0, n_labels) sets WTHETA_DERR_LABEL and counts as 0.
+__global__ void k_sorted_labels(const unsigned* __restrict__ order, const int* __restrict__ labels,
+                                long long n, int n_labels, unsigned* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        int l = labels[order[i]];
+        if (l < 0 || l >= n_labels) {
+            atomicOr(&g_device_error, WTHETA_DERR_LABEL);
+            l = 0;
+        }
+        out[i] = (unsigned)l;
+    }
+}
+
+// sizes[l] = number of points with label l (labels sorted or not).
+__global__ void k_count_labels(const unsigned* __restrict__ lab, long long n, int n_labels,
+                               unsigned long long* __restrict__ sizes) {
+    __shared__ unsigned c[256];
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) c[q] = 0;
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&c[lab[i] & 255u], 1u);
+    __syncthreads();
+    for (int q = threadIdx.x; q < n_labels; q += blockDim.x)
+        if (c[q]) atomicAdd(sizes + q, (unsigned long long)c[q]);
+}
+
+// FP32 copies with every region starting on a tile boundary: region r's
+// points (sorted positions src[r] .. src[r+1]-1) go to dst[r] .., the rest of
+// its last tile holds sentinels.  dst[R] = n_pad.
+__global__ void k_gather_regions(const double* __restrict__ xyz, long long stride,
+                                 const unsigned* __restrict__ order,
+                                 const long long* __restrict__ src,
+                                 const long long* __restrict__ dst, int R, long long n_pad,
+                                 float4* __restrict__ p32, int tag) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
+         i += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = R - 1;  // last region with dst <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (dst[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const long long j = i - dst[lo];
+        if (j < src[lo + 1] - src[lo]) {
+            const long long k = order[src[lo] + j];
+            p32[i] = point32(xyz[k], xyz[stride + k], xyz[2 * stride + k], k);
+        } else {
+            p32[i] = sentinel32(tag, i);
+        }
+    }
+}
+
 // acc[k] += add[k] for the K+2 slots (combining two counts of one shard).
 __global__ void k_add_counts(unsigned long long* acc, const unsigned long long* add, int n) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) acc[k] += add[k];
@@ -395,40 +451,52 @@ __device__ __forceinline__ void item_to_tiles(long long t, long long T_a, long l
     *J = i + (t - (i * T - i * (i - 1) / 2));
 }
 
-// Bounding cap of each tile of T spatially ordered FP32 points (real points
-// are [0, n), padding after): centre = normalised FP64 sum, radius = the
-// largest angle from the centre, plus 1e-6 rad for the FP32 rounding of the
-// points (a point moves by at most ~1.1e-7 rad from its FP64 position).
+// Bounding cap of each tile of T spatially ordered FP32 points (positions
+// [0, n); padding sentinels, far off the unit sphere, are left out):
+// centre = normalised FP64 sum, radius = the largest angle from the centre,
+// plus 1e-6 rad for the FP32 rounding of the points (a point moves by at most
+// ~1.1e-7 rad from its FP64 position).
+__device__ __forceinline__ bool is_sentinel(const float4& q) {
+    return q.x * q.x + q.y * q.y + q.z * q.z > 4.f;
+}
+
 __global__ void __launch_bounds__(128) k_tile_caps(const float4* __restrict__ p32, long long n,
                                                    int T, TileCap* __restrict__ caps) {
     __shared__ double red[4][4];
+    __shared__ int cnt[4];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long t0 = (long long)blockIdx.x * T;
     const long long t1 = min(t0 + (long long)T, n);
     double sx = 0, sy = 0, sz = 0;
+    int c = 0;
     for (long long i = t0 + tid; i < t1; i += blockDim.x) {
         const float4 q = p32[i];
+        if (is_sentinel(q)) continue;
         sx += q.x; sy += q.y; sz += q.z;
+        ++c;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         sx += __shfl_xor_sync(0xffffffffu, sx, o);
         sy += __shfl_xor_sync(0xffffffffu, sy, o);
         sz += __shfl_xor_sync(0xffffffffu, sz, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
     }
-    if (lane == 0) { red[warp][0] = sx; red[warp][1] = sy; red[warp][2] = sz; }
+    if (lane == 0) { red[warp][0] = sx; red[warp][1] = sy; red[warp][2] = sz; cnt[warp] = c; }
     __syncthreads();
     sx = red[0][0] + red[1][0] + red[2][0] + red[3][0];
     sy = red[0][1] + red[1][1] + red[2][1] + red[3][1];
     sz = red[0][2] + red[1][2] + red[2][2] + red[3][2];
+    c = cnt[0] + cnt[1] + cnt[2] + cnt[3];
     const double nrm = sqrt(sx * sx + sy * sy + sz * sz);
-    const bool empty = t1 <= t0;
-    const bool spread = !(nrm > 1e-3 * (double)(t1 - t0));  // centre ill-defined: no skipping
+    const bool empty = c == 0;
+    const bool spread = !(nrm > 1e-3 * (double)c);  // centre ill-defined: no skipping
     const double cx = spread ? 1.0 : sx / nrm, cy = spread ? 0.0 : sy / nrm,
                  cz = spread ? 0.0 : sz / nrm;
     double m = 0;
     for (long long i = t0 + tid; i < t1; i += blockDim.x) {
         const float4 q = p32[i];
+        if (is_sentinel(q)) continue;
         const double dx = cx - q.x, dy = cy - q.y, dz = cz - q.z;
         m = fmax(m, dx * dx + dy * dy + dz * dz);
     }
@@ -439,19 +507,20 @@ __global__ void __launch_bounds__(128) k_tile_caps(const float4* __restrict__ p3
     __syncthreads();
     if (tid == 0) {
         m = fmax(fmax(red[0][3], red[1][3]), fmax(red[2][3], red[3][3]));
-        TileCap c;
-        c.x = cx; c.y = cy; c.z = cz;
-        c.rho = empty ? -1.0
-                      : (spread ? 4.0 : 2.0 * asin(fmin(1.0, 0.5 * sqrt(m))) + 1e-6);
-        caps[blockIdx.x] = c;
+        TileCap cap;
+        cap.x = cx; cap.y = cy; cap.z = cz;
+        cap.rho = empty ? -1.0
+                        : (spread ? 4.0 : 2.0 * asin(fmin(1.0, 0.5 * sqrt(m))) + 1e-6);
+        caps[blockIdx.x] = cap;
     }
 }
 
 // Bounding sphere of every chunk of 32 consecutive spatially ordered FP32
 // points: centre = the FP32 mean of the chunk's points, radius = the largest
 // FP32 distance of a point from it, enlarged by a relative 1e-6 for the few
-// roundings of that arithmetic.  A chunk holding a padding point gets radius
-// -1, so that its pairs are never settled per chunk.  One warp per chunk.
+// roundings of that arithmetic.  A chunk holding a padding sentinel gets
+// radius -1, so that its pairs are never settled per chunk.  One warp per
+// chunk.
 __global__ void k_chunk_caps(const float4* __restrict__ p32, long long n, long long n_pad,
                              float4* __restrict__ caps) {
     const int lane = threadIdx.x & 31;
@@ -473,7 +542,7 @@ __global__ void k_chunk_caps(const float4* __restrict__ p32, long long n, long l
         float m = dx * dx + dy * dy + dz * dz;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        const bool pad = __any_sync(0xffffffffu, i >= n);
+        const bool pad = __any_sync(0xffffffffu, i >= n || is_sentinel(q));
         if (lane == 0) caps[c] = make_float4(cx, cy, cz, pad ? -1.f : sqrtf(m) * (1.f + 1e-6f));
     }
 }
@@ -606,6 +675,7 @@ struct PairKernel {
         b += (size_t)TB / 32 * 16;              // bounding spheres of its 32-point chunks
         b += (size_t)n_lut * 16;                // screening table
         b += (size_t)(K + 2) * 8;               // FP64 edges (+ pad)
+        b += (size_t)(K + 2) * 8;               // guard band of every edge
         b += (size_t)(K + 2) * HCOLS * 4;       // histograms, row K+1 a trash row
         return b;
     }
@@ -697,13 +767,14 @@ __device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsign
 }
 
 // Squared chords of JU consecutive B points (from j) with the thread's R A
-// points: s[h R + r].  On a diagonal tile, pairs with i >= j get +inf.  The
-// B tile sits at shared addresses bxy (16 B per point: -x,-x,-y,-y) and
+// points: s[h R + r].  On a diagonal tile, pairs with i >= j get +inf, i
+// being a_first + r (the thread's first A point's position in the tile).
+// The B tile sits at shared addresses bxy (16 B per point: -x,-x,-y,-y) and
 // bz (8 B per point: -z,-z).
 template <int NT, int R, int JU, bool DIAG>
 __device__ __forceinline__ void chords(float (&s)[JU * R], unsigned bxy_base, unsigned bz_base,
                                        const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
-                                       const f2_t (&az)[R / 2], int j) {
+                                       const f2_t (&az)[R / 2], int j, int a_first) {
 #pragma unroll
     for (int h = 0; h < JU; ++h) {
         f2_t bx, by;
@@ -723,7 +794,7 @@ __device__ __forceinline__ void chords(float (&s)[JU * R], unsigned bxy_base, un
         for (int h = 0; h < JU; ++h)
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                if (j + h <= (int)threadIdx.x * R + r) s[h * R + r] = __int_as_float(0x7f800000);
+                if (j + h <= a_first + r) s[h * R + r] = __int_as_float(0x7f800000);
     }
 }
 
@@ -745,18 +816,18 @@ __device__ __forceinline__ void exact_steps(int j0, int j1, unsigned bxy, unsign
                                             const f2_t (&ay)[R / 2], const f2_t (&az)[R / 2],
                                             float hf, int shift, int base, int top_idx,
                                             unsigned row_bytes, int K, const Segment& S,
-                                            long long a0, long long b0,
+                                            long long a0, long long b0, int a_first,
                                             unsigned long long& n_recheck) {
     constexpr int NV = JU * R;
 #pragma unroll 1
     for (int j = j0; j < j1; j += JU) {
         float s[NV];
-        chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
+        chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j, a_first);
         const float m = min_of(s);
         if (!(m <= hf)) continue;
         if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx)) {
             float s2[NV];
-            chords<NT, R, JU, DIAG>(s2, bxy, bz, ax, ay, az, j);
+            chords<NT, R, JU, DIAG>(s2, bxy, bz, ax, ay, az, j, a_first);
             recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, row_bytes, K,
                                                S, a0, b0 + j, sC, n_recheck);
         }
@@ -798,12 +869,17 @@ __device__ __forceinline__ float4 group_cap(const f2_t (&ax)[R / 2], const f2_t 
 // classifies both ends (values inside a guard band or a bucket with several
 // edges are ambiguous):
 //   0  both ends in one slot: every pair is in slot rlo;
-//   1  adjacent slots split by the edge of `edge` (its guard band [x, y]):
-//      each pair is in rlo or rhi by one FP32 comparison, outside the band;
+//   1  adjacent slots k and k+1, split by edge k alone (its guard band
+//      [x, y] from the band table at shared address band): each pair is in
+//      rlo or rhi by one FP32 comparison, outside the band;
+//   3  slots k, k+1, k+2, split by edges k (edge) and k+1 (edge2): two
+//      comparisons per pair;
 //   2  anything else: bin pair by pair.
+// Rows are byte offsets of slots, slot << row_shift.
 __device__ __forceinline__ int span_mode(float4 ga, float4 gb, unsigned lut, int shift, int base,
-                                         int top_idx, unsigned& rlo, unsigned& rhi,
-                                         uint4& edge) {
+                                         int top_idx, unsigned band, int row_shift,
+                                         unsigned& rlo, unsigned& rhi, uint2& edge,
+                                         uint2& edge2) {
     const float dx = ga.x - gb.x, dy = ga.y - gb.y, dz = ga.z - gb.z;
     const float dc = sqrtf(dx * dx + dy * dy + dz * dz);
     const float rr = (ga.w + gb.w) * (1.f + 1e-6f) + 1e-6f;
@@ -818,26 +894,63 @@ __device__ __forceinline__ int span_mode(float4 ga, float4 gb, unsigned lut, int
     rlo = bl < el.x ? el.z : el.w;
     rhi = bh < eh.x ? eh.z : eh.w;
     if (rlo == rhi) return 0;
-    if (eh.z == rlo && eh.w == rhi) { edge = eh; return 1; }
-    if (el.z == rlo && el.w == rhi) { edge = el; return 1; }
+    if (rhi == rlo + (1u << row_shift) || rhi == rlo + (2u << row_shift)) {
+        const unsigned a = band + 8u * (rlo >> row_shift);
+        unsigned lo, hi;
+        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(a));
+        edge = make_uint2(lo, hi);
+        if (rhi == rlo + (1u << row_shift)) return 1;
+        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(a + 8u));
+        edge2 = make_uint2(lo, hi);
+        return 3;
+    }
     return 2;
 }
 
-// One step of a two-slot chunk: the squared chords of JU B points with the
-// thread's R A points, computed exactly as in chords(), then d = s - mid.
-// neg counts the values with d < 0; mb keeps the smallest |d|.
+// One step of a three-slot chunk: as two_slot_step, against two edges (the
+// middles of their guard bands mid1 < mid2), with one accumulator each.
 template <int R, int JU>
-__device__ __forceinline__ void two_slot_step(unsigned bxy_base, unsigned bz_base,
-                                              const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
-                                              const f2_t (&az)[R / 2], int j, f2_t nmid,
-                                              unsigned& neg, float& mb) {
+__device__ __forceinline__ void three_slot_step(unsigned bxy_base, unsigned bz_base,
+                                                const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
+                                                const f2_t (&az)[R / 2], int j, f2_t nmid1,
+                                                f2_t nmid2, unsigned& neg1, unsigned& neg2,
+                                                float& mb1, float& mb2) {
 #pragma unroll
     for (int h = 0; h < JU; ++h) {
         f2_t bx, by;
         lds_f2x2(bxy_base + 16u * (unsigned)(j + h), bx, by);
         const f2_t bz = lds_f2(bz_base + 8u * (unsigned)(j + h));
-        float m = mb;
-        unsigned c = 0;
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) {
+            const f2_t dx = add2(ax[q], bx);
+            const f2_t dy = add2(ay[q], by);
+            const f2_t dz = add2(az[q], bz);
+            const f2_t t = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+            float d0, d1, e0, e1;
+            unpack2(add2(t, nmid1), d0, d1);
+            unpack2(add2(t, nmid2), e0, e1);
+            mb1 = min3f(mb1, fabsf(d0), fabsf(d1));
+            mb2 = min3f(mb2, fabsf(e0), fabsf(e1));
+            neg1 += (__float_as_uint(d0) >> 31) + (__float_as_uint(d1) >> 31);
+            neg2 += (__float_as_uint(e0) >> 31) + (__float_as_uint(e1) >> 31);
+        }
+    }
+}
+
+// One step of a two-slot chunk: the squared chords of JU B points with the
+// thread's R A points, computed exactly as in chords(), then d = s - mid.
+// neg[q] counts the values with d < 0 and mb[q] keeps the smallest |d|, one
+// accumulator per A pair q so that the steps' dependency chains interleave.
+template <int R, int JU>
+__device__ __forceinline__ void two_slot_step(unsigned bxy_base, unsigned bz_base,
+                                              const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
+                                              const f2_t (&az)[R / 2], int j, f2_t nmid,
+                                              unsigned (&neg)[R / 2], float (&mb)[R / 2]) {
+#pragma unroll
+    for (int h = 0; h < JU; ++h) {
+        f2_t bx, by;
+        lds_f2x2(bxy_base + 16u * (unsigned)(j + h), bx, by);
+        const f2_t bz = lds_f2(bz_base + 8u * (unsigned)(j + h));
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) {
             const f2_t dx = add2(ax[q], bx);
@@ -846,20 +959,22 @@ __device__ __forceinline__ void two_slot_step(unsigned bxy_base, unsigned bz_bas
             const f2_t t = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
             float d0, d1;
             unpack2(add2(t, nmid), d0, d1);
-            m = min3f(m, fabsf(d0), fabsf(d1));
-            c += (__float_as_uint(d0) >> 31) + (__float_as_uint(d1) >> 31);
+            mb[q] = min3f(mb[q], fabsf(d0), fabsf(d1));
+            neg[q] += (__float_as_uint(d0) >> 31) + (__float_as_uint(d1) >> 31);
         }
-        mb = m;
-        neg += c;
     }
 }
 
+// The pairs of the thread's R A points (tile positions a_first ..) with the
+// B points [j_begin, j_end) of the staged tile.
 template <int NT, int R, int JU, int HM, int DEF, bool DIAG>
 __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lut, unsigned caps,
-                                          const double* __restrict__ sC, unsigned hist,
+                                          unsigned band, const double* __restrict__ sC,
+                                          unsigned hist,
                                           const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
-                                          const f2_t (&az)[R / 2], const PairParams& p,
-                                          const Segment& S, long long I, long long J,
+                                          const f2_t (&az)[R / 2], const float4& ga,
+                                          const PairParams& p, const Segment& S, long long I,
+                                          long long J, int a_first, int j_begin, int j_end,
                                           unsigned long long& n_recheck,
                                           unsigned long long& n_span,
                                           unsigned long long& n_skip) {
@@ -871,21 +986,23 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
     const float hf = __uint_as_float(h_top);
     const int shift = p.tab.shift, base = p.tab.base, K = p.tab.K, top_idx = p.tab.n_lut - 1;
     const unsigned row_bytes = HCOLS * 4u;
+    constexpr int row_shift = ilog2(HCOLS * 4);
+    static_assert((1 << row_shift) == HCOLS * 4, "rows are a power of two bytes");
     const unsigned col = hist + 4u * (unsigned)(HM == kHistWarp ? warp : tid);
-    const long long a0 = I * TA + (long long)tid * R, b0 = J * TB;
+    const long long a0 = I * TA + a_first, b0 = J * TB;
 
     if (DEF) {
         // Deferred binning: the screening loop only notes, one bit per step,
         // which of 32 consecutive steps hold an in-range value; those steps
         // are then recomputed and binned.  The screening loop stays small.
-        static_assert(TB % (32 * JU) == 0, "tile must hold whole 32-step blocks");
+        static_assert(TB % (4 * 32 * JU) == 0, "units must hold whole 32-step blocks");
 #pragma unroll 1
-        for (int jb = 0; jb < TB; jb += 32 * JU) {
+        for (int jb = j_begin; jb < j_end; jb += 32 * JU) {
             unsigned mask = 0;
 #pragma unroll 1
             for (int st = 0; st < 32; ++st) {
                 float s[NV];
-                chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, jb + st * JU);
+                chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, jb + st * JU, a_first);
                 mask |= (min_of(s) <= hf ? 1u : 0u) << st;
             }
             while (mask) {
@@ -893,7 +1010,7 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
                 mask &= mask - 1;
                 const int j = jb + st * JU;
                 float s[NV];
-                chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
+                chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j, a_first);
                 if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx))
                     recount_band_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx,
                                                        row_bytes, K, S, a0, b0 + j, sC, n_recheck);
@@ -902,9 +1019,9 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
         return;
     } else if (HM == kHistWarp) {
 #pragma unroll 1
-        for (int j = 0; j < TB; j += JU) {
+        for (int j = j_begin; j < j_end; j += JU) {
             float s[NV];
-            chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j);
+            chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j, a_first);
             const float m = min_of(s);
             if (!__any_sync(0xffffffffu, m <= hf)) continue;
             const unsigned trash = (unsigned)(K + 1) * row_bytes;
@@ -930,28 +1047,29 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
         return;
     }
     if (DIAG || !p.span || !S.b_caps) {
-        exact_steps<NT, R, JU, HM, DIAG>(0, TB, bxy, bz, lut, sC, col, ax, ay, az, hf, shift, base,
-                                         top_idx, row_bytes, K, S, a0, b0, n_recheck);
+        exact_steps<NT, R, JU, HM, DIAG>(j_begin, j_end, bxy, bz, lut, sC, col, ax, ay, az, hf,
+                                         shift, base, top_idx, row_bytes, K, S, a0, b0, a_first,
+                                         n_recheck);
         return;
     }
     // Chunks of 32 B points: the warp bins a chunk pair by pair only if one
     // of its threads has to; otherwise each thread settles its A points
     // against the chunk in one slot or with one comparison per pair.
     constexpr int CH = 32;
-    static_assert(TB % CH == 0 && CH % JU == 0, "whole chunks");
-    const float4 ga = group_cap<R>(ax, ay, az);
+    static_assert(TB % (4 * CH) == 0 && CH % JU == 0, "whole chunks");
 #pragma unroll 1
-    for (int c0 = 0; c0 < TB; c0 += CH) {
+    for (int c0 = j_begin; c0 < j_end; c0 += CH) {
         const uint4 gbu = lds_u4(caps + 16u * (unsigned)(c0 / CH));
         const float4 gb = make_float4(__uint_as_float(gbu.x), __uint_as_float(gbu.y),
                                       __uint_as_float(gbu.z), __uint_as_float(gbu.w));
         unsigned rlo = 0, rhi = 0;
-        uint4 edge = make_uint4(0u, 0u, 0u, 0u);
-        const int mode = span_mode(ga, gb, lut, shift, base, top_idx, rlo, rhi, edge);
+        uint2 edge = make_uint2(0u, 0u), edge2 = make_uint2(0x7f800000u, 0x7f800000u);
+        const int mode = span_mode(ga, gb, lut, shift, base, top_idx, band, row_shift, rlo, rhi,
+                                   edge, edge2);
         if (__any_sync(0xffffffffu, mode == 2)) {
             exact_steps<NT, R, JU, HM, false>(c0, c0 + CH, bxy, bz, lut, sC, col, ax, ay, az, hf,
                                               shift, base, top_idx, row_bytes, K, S, a0, b0,
-                                              n_recheck);
+                                              a_first, n_recheck);
             continue;
         }
         if (mode == 0) {
@@ -969,16 +1087,57 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
         const float mid = 0.5f * (lo_f + hi_f);
         const float G = fmaxf(mid - lo_f, hi_f - mid);
         const f2_t nmid = pack2(-mid, -mid);
+        if (__any_sync(0xffffffffu, mode == 3)) {
+            // Three slots for some thread: a second edge (+inf for the others,
+            // whose second count is then zero).
+            const float lo2 = __uint_as_float(edge2.x), hi2 = __uint_as_float(edge2.y);
+            const float mid2 = 0.5f * (lo2 + hi2);
+            const float G2 = fmaxf(mid2 - lo2, hi2 - mid2);
+            unsigned neg1 = 0, neg2 = 0;
+            float mb1 = __int_as_float(0x7f800000), mb2 = __int_as_float(0x7f800000);
+#pragma unroll 2
+            for (int j = c0; j < c0 + CH; j += JU)
+                three_slot_step<R, JU>(bxy, bz, ax, ay, az, j, nmid, pack2(-mid2, -mid2), neg1,
+                                       neg2, mb1, mb2);
+            if (mode == 1 || mode == 3) {
+                if (mb1 <= G || (mode == 3 && mb2 <= G2)) {
+                    exact_steps<NT, R, JU, HM, false>(c0, c0 + CH, bxy, bz, lut, sC, col, ax, ay,
+                                                      az, hf, shift, base, top_idx, row_bytes, K,
+                                                      S, a0, b0, a_first, n_recheck);
+                } else {
+                    const unsigned ge1 = (unsigned)(R * CH) - neg1;
+                    const unsigned ge2 = mode == 3 ? (unsigned)(R * CH) - neg2 : 0u;
+                    hist_add<HM>(col + rlo, neg1);
+                    hist_add<HM>(col + rlo + row_bytes, ge1 - ge2);
+                    if (mode == 3) hist_add<HM>(col + rhi, ge2);
+                    n_span += R * CH;
+                }
+            }
+            continue;
+        }
+        unsigned negq[R / 2];
+        float mbq[R / 2];
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) {
+            negq[q] = 0;
+            mbq[q] = __int_as_float(0x7f800000);
+        }
+#pragma unroll 2
+        for (int j = c0; j < c0 + CH; j += JU)
+            two_slot_step<R, JU>(bxy, bz, ax, ay, az, j, nmid, negq, mbq);
         unsigned neg = 0;
         float mb = __int_as_float(0x7f800000);
-#pragma unroll 2
-        for (int j = c0; j < c0 + CH; j += JU) two_slot_step<R, JU>(bxy, bz, ax, ay, az, j, nmid, neg, mb);
+#pragma unroll
+        for (int q = 0; q < R / 2; ++q) {
+            neg += negq[q];
+            mb = fminf(mb, mbq[q]);
+        }
         if (mode == 1) {
             if (mb <= G) {
                 // rare: a value near the edge; this thread bins the chunk pair by pair
                 exact_steps<NT, R, JU, HM, false>(c0, c0 + CH, bxy, bz, lut, sC, col, ax, ay, az,
                                                   hf, shift, base, top_idx, row_bytes, K, S, a0,
-                                                  b0, n_recheck);
+                                                  b0, a_first, n_recheck);
             } else {
                 hist_add<HM>(col + rlo, neg);
                 hist_add<HM>(col + rhi, (unsigned)(R * CH) - neg);
@@ -989,9 +1148,12 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
 }
 
 template <int NT, int R, int JU, int HM, int DEF>
-__global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams p) {
+__global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __grid_constant__ PairParams p) {
     using PK = PairKernel<NT, R, JU, HM, DEF>;
     constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
+    constexpr int NW = NT / 32, SA = 32 * R, UPS = 4, UB = TB / UPS;
+    static_assert(TA == NW * SA && TB % UPS == 0, "units tile the item");
+    __shared__ unsigned s_units[NW];
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.tab.K;
     ulonglong2* sBxy = reinterpret_cast<ulonglong2*>(smem);
@@ -999,7 +1161,8 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
     float4* sCap = reinterpret_cast<float4*>(sBz + TB);
     uint4* sLut = reinterpret_cast<uint4*>(sCap + TB / 32);
     double* sC = reinterpret_cast<double*>(sLut + p.tab.n_lut);
-    unsigned* hist = reinterpret_cast<unsigned*>(sC + (K + 2));
+    uint2* sBand = reinterpret_cast<uint2*>(sC + (K + 2));
+    unsigned* hist = reinterpret_cast<unsigned*>(sBand + (K + 2));
     __shared__ long long s_item, s_I, s_J;
 
     const int tid = threadIdx.x;
@@ -1007,7 +1170,10 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
     for (int q = tid; q < p.tab.n_lut; q += NT)
         sLut[q] = make_uint4(p.tab.lut[q][0], p.tab.lut[q][1], p.tab.lut[q][2] * row_bytes,
                              p.tab.lut[q][3] * row_bytes);
-    for (int q = tid; q <= K; q += NT) sC[q] = p.tab.c64[q];
+    for (int q = tid; q <= K; q += NT) {
+        sC[q] = p.tab.c64[q];
+        sBand[q] = make_uint2(p.tab.band[q][0], p.tab.band[q][1]);
+    }
     for (int q = tid; q < (K + 2) * HCOLS; q += NT) hist[q] = 0u;
 
     // the current count lives in shared memory; thread 0 switches it when an
@@ -1071,33 +1237,65 @@ __global__ void __launch_bounds__(NT) k_pairs(const __grid_constant__ PairParams
         }
         if (S.b_caps)
             for (int q = tid; q < TB / 32; q += NT) sCap[q] = S.b_caps[J * (TB / 32) + q];
-        // The thread's A points are R consecutive points of the spatial order
-        // (a compact group: see span_mode), packed two by two for the FP32x2
-        // instructions.
-        // Each value goes through an explicit add of +0 (exact; it only turns
-        // -0 into +0, which leaves every squared chord unchanged): the packed
-        // operands then get registers of their own instead of being formed in
-        // place from the vector-load destinations, a layout measured to cost
-        // about a quarter of the screening loop's throughput.
-        f2_t ax[R / 2], ay[R / 2], az[R / 2];
-        const float4* gA = S.a32 + I * TA;
-#pragma unroll
-        for (int q = 0; q < R / 2; ++q) {
-            const float4 u = gA[tid * R + 2 * q];
-            const float4 v = gA[tid * R + 2 * q + 1];
-            ax[q] = pack2(__fadd_rn(u.x, 0.f), __fadd_rn(v.x, 0.f));
-            ay[q] = pack2(__fadd_rn(u.y, 0.f), __fadd_rn(v.y, 0.f));
-            az[q] = pack2(__fadd_rn(u.z, 0.f), __fadd_rn(v.z, 0.f));
-        }
-        __syncthreads();  // B tile staged
+        if (tid < NW) s_units[tid] = 0;
+        __syncthreads();  // B tile staged, unit counters reset
         const unsigned a_bxy = smem_addr(sBxy), a_bz = smem_addr(sBz), a_lut = smem_addr(sLut),
-                       a_cap = smem_addr(sCap), a_hist = smem_addr(hist);
-        if (S.is_auto && I == J)
-            tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, a_cap, sC, a_hist, ax, ay, az,
-                                                p, S, I, J, n_recheck, n_span, n_skip);
-        else
-            tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, a_cap, sC, a_hist, ax, ay, az,
-                                                 p, S, I, J, n_recheck, n_span, n_skip);
+                       a_cap = smem_addr(sCap), a_band = smem_addr(sBand),
+                       a_hist = smem_addr(hist);
+        // The item is split into units of one warp's worth of A points (SA =
+        // 32 R consecutive points, a sub-tile) by a quarter of the B tile.  A
+        // warp takes the units of its own sub-tile first, then those left of
+        // the others, so the warps of the block finish the item together
+        // whatever the mix of cheap and costly units.
+        const int lane = tid & 31, warp = tid >> 5;
+        const bool diag = S.is_auto && I == J;
+        int cur = -1;
+        f2_t ax[R / 2], ay[R / 2], az[R / 2];
+        float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+        for (int k = 0; k < NW; ++k) {
+            const int sub = (warp + k) % NW;
+#pragma unroll 1
+            for (;;) {
+                unsigned u = 0;
+                if (lane == 0) u = atomicAdd(&s_units[sub], 1u);
+                u = __shfl_sync(0xffffffffu, u, 0);
+                if (u >= (unsigned)UPS) break;
+                const int a_first = sub * SA + lane * R;
+                const int jb = (int)u * UB, je = jb + UB;
+                if (diag && je <= sub * SA) continue;  // every pair has i >= j
+                if (sub != cur) {
+                    // The thread's A points are R consecutive points of the
+                    // spatial order (a compact group: see span_mode), packed
+                    // two by two for the FP32x2 instructions.  Each value goes
+                    // through an explicit add of +0 (exact; it only turns -0
+                    // into +0, which leaves every squared chord unchanged): the
+                    // packed operands then get registers of their own instead
+                    // of being formed in place from the vector-load
+                    // destinations, a layout measured to cost about a quarter
+                    // of the screening loop's throughput.
+                    const float4* gA = S.a32 + I * TA + a_first;
+#pragma unroll
+                    for (int q = 0; q < R / 2; ++q) {
+                        const float4 a = gA[2 * q];
+                        const float4 b = gA[2 * q + 1];
+                        ax[q] = pack2(__fadd_rn(a.x, 0.f), __fadd_rn(b.x, 0.f));
+                        ay[q] = pack2(__fadd_rn(a.y, 0.f), __fadd_rn(b.y, 0.f));
+                        az[q] = pack2(__fadd_rn(a.z, 0.f), __fadd_rn(b.z, 0.f));
+                    }
+                    ga = group_cap<R>(ax, ay, az);
+                    cur = sub;
+                }
+                if (diag && jb < (sub + 1) * SA)
+                    tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, a_cap, a_band, sC, a_hist, ax,
+                                                        ay, az, ga, p, S, I, J, a_first, jb, je,
+                                                        n_recheck, n_span, n_skip);
+                else
+                    tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, a_cap, a_band, sC, a_hist, ax,
+                                                         ay, az, ga, p, S, I, J, a_first, jb, je,
+                                                         n_recheck, n_span, n_skip);
+            }
+        }
         ++n_items;
         if (++since_flush == p.items_per_flush) {
             __syncthreads();
@@ -1252,30 +1450,67 @@ static long long sort_blocks(long long n) {
     return std::max<long long>(1, (n + kSortTile - 1) / kSortTile);
 }
 
-size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
+size_t order_bytes(long long n, int with_labels) {
     const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
+    return (4 + (with_labels ? 1 : 0)) * a4 +                   // keys, indices (x2), labels
+           ((size_t)sort_blocks(n) * 256 * 4 + 255) / 256 * 256;  // digit counts per block
+}
+
+int spatial_order(const double* x64, long long stride, long long n, int check,
+                  const int* labels, int n_labels, unsigned char* scratch, int sm_count,
+                  cudaStream_t st, const unsigned** order, const unsigned** sorted_labels) {
+    const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
+    const long long G = sort_blocks(n);
+    unsigned* key[2] = {(unsigned*)scratch, (unsigned*)(scratch + a4)};
+    unsigned* idx[2] = {(unsigned*)(scratch + 2 * a4), (unsigned*)(scratch + 3 * a4)};
+    unsigned* lab = (unsigned*)(scratch + 4 * a4);
+    unsigned* hist = (unsigned*)(scratch + (4 + (labels ? 1 : 0)) * a4);
+    *order = idx[0];
+    if (sorted_labels) *sorted_labels = nullptr;
+    if (n <= 0) return WTHETA_OK;
+    k_sort_keys<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, check, key[0], idx[0]);
+    count_launch();
+    for (int pass = 0; pass < 4; ++pass) {
+        const int in = pass & 1, o = in ^ 1;
+        k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], n, 8 * pass, hist);
+        k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
+        k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], idx[in], n, 8 * pass, hist,
+                                                              key[o], idx[o]);
+        count_launch(3);
+    }
+    // four passes: the order is back in the first buffers
+    if (labels) {
+        // one more stable pass, on the label: regions in label order, each in
+        // spatial order
+        k_sorted_labels<<<launch_grid(n, sm_count), 256, 0, st>>>(idx[0], labels, n, n_labels, lab);
+        k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(lab, n, 0, hist);
+        k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
+        k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(lab, idx[0], n, 0, hist, key[1],
+                                                              idx[1]);
+        count_launch(4);
+        *order = idx[1];
+        if (sorted_labels) *sorted_labels = key[1];
+    }
+    return check_cuda(cudaGetLastError());
+}
+
+size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
     size_t b = (size_t)n_pad * 16 + 256;               // FP32 points
     b += ((size_t)n_pad / 32 * 16 + 255) / 256 * 256;  // chunk bounding spheres
-    b += 4 * a4;                                       // keys and indices, two buffers each
-    b += ((size_t)sort_blocks(n) * 256 * 4 + 255) / 256 * 256;  // digit counts per block
-    if (!is_xyz) b += ((size_t)n * 24 + 255) / 256 * 256;      // FP64 SoA
+    b += order_bytes(n, 0);                            // the sort
+    if (!is_xyz) b += ((size_t)n * 24 + 255) / 256 * 256;  // FP64 SoA
     return b;
 }
 
 int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int tag,
                    unsigned char* scratch, int sm_count, cudaStream_t st, Prepared* out) {
-    const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
-    const long long G = sort_blocks(n);
     unsigned char* sp = scratch;
     float4* p32 = (float4*)sp;
     sp += ((size_t)n_pad * 16 + 255) / 256 * 256;
     float4* c32 = (float4*)sp;
     sp += ((size_t)n_pad / 32 * 16 + 255) / 256 * 256;
-    unsigned* key[2] = {(unsigned*)sp, (unsigned*)(sp + a4)};
-    unsigned* idx[2] = {(unsigned*)(sp + 2 * a4), (unsigned*)(sp + 3 * a4)};
-    sp += 4 * a4;
-    unsigned* hist = (unsigned*)sp;
-    sp += ((size_t)G * 256 * 4 + 255) / 256 * 256;
+    unsigned char* sort_scratch = sp;
+    sp += order_bytes(n, 0);
     const double* x64 = coords;
     long long stride = n;
     if (!is_xyz && n > 0) {
@@ -1284,21 +1519,11 @@ int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int 
         count_launch();
         x64 = x;
     }
-    if (n > 0) {
-        k_sort_keys<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, is_xyz, key[0],
-                                                                idx[0]);
-        count_launch();
-        for (int pass = 0; pass < 4; ++pass) {
-            const int in = pass & 1, o = in ^ 1;
-            k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], n, 8 * pass, hist);
-            k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
-            k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], idx[in], n, 8 * pass,
-                                                                  hist, key[o], idx[o]);
-            count_launch(3);
-        }
-    }
-    // four passes: the order is back in the first buffers
-    k_gather_points<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(x64, stride, n, n_pad, idx[0],
+    const unsigned* order = nullptr;
+    int rc = spatial_order(x64, stride, n, is_xyz, nullptr, 0, sort_scratch, sm_count, st, &order,
+                           nullptr);
+    if (rc) return rc;
+    k_gather_points<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(x64, stride, n, n_pad, order,
                                                                   p32, tag);
     k_chunk_caps<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(p32, n, n_pad, c32);
     count_launch(2);
@@ -1309,11 +1534,58 @@ int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int 
     return check_cuda(cudaGetLastError());
 }
 
+int launch_radec_to_xyz(const double* coords, long long n, double* xyz, int sm_count,
+                        cudaStream_t st) {
+    if (n <= 0) return WTHETA_OK;
+    k_radec_to_xyz<<<launch_grid(n, sm_count), 256, 0, st>>>(coords, n, xyz, n);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_count_labels(const unsigned* lab, long long n, int n_labels,
+                        unsigned long long* sizes, int sm_count, cudaStream_t st) {
+    if (n <= 0) return WTHETA_OK;
+    k_count_labels<<<launch_grid(n, sm_count), 256, 0, st>>>(lab, n, n_labels, sizes);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_gather_regions(const double* x64, long long stride, const unsigned* order,
+                          const long long* src, const long long* dst, int R, long long n_pad,
+                          float4* p32, int tag, int sm_count, cudaStream_t st) {
+    if (n_pad <= 0) return WTHETA_OK;
+    k_gather_regions<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(x64, stride, order, src, dst,
+                                                                   R, n_pad, p32, tag);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_chunk_caps(const float4* p32, long long n_pad, float4* c32, int sm_count,
+                      cudaStream_t st) {
+    if (n_pad <= 0) return WTHETA_OK;
+    k_chunk_caps<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(p32, n_pad, n_pad, c32);
+    count_launch();
+    return check_cuda(cudaGetLastError());
+}
+
+int launch_cull_batch(const CullSeg* cs, int n_segs, long long total, double theta_top,
+                      unsigned long long* kept, Segment* segs, unsigned long long* n_kept,
+                      int sm_count, cudaStream_t st) {
+    if (n_segs <= 0) return WTHETA_OK;
+    k_cull_batch<<<launch_grid(std::max(total, 1LL), sm_count), 256, 0, st>>>(cs, n_segs, total,
+                                                                             theta_top, kept);
+    k_cull_prefix<<<1, 32, 0, st>>>(segs, cs, kept, n_segs, n_kept);
+    count_launch(2);
+    return check_cuda(cudaGetLastError());
+}
+
 unsigned long long per_item_bound(const Variant* v) {
-    // a thread evaluates R x TB pairs per item, so a histogram cell gains at
-    // most R TB (private per-thread column) or 32 R TB (per-warp column)
-    return (v->hm == kHistWarp ? 32ull : 1ull) * (unsigned long long)v->r *
-           (unsigned long long)v->nt * (unsigned long long)v->r;
+    // a thread evaluates R x TB pairs per unit of its own sub-tile and may
+    // take the units of every other sub-tile of the item (NT/32 of them), so
+    // a histogram cell gains at most NT/32 x R TB per item (private
+    // per-thread column), 32 times that for a per-warp column
+    return (v->hm == kHistWarp ? 32ull : 1ull) * (unsigned long long)(v->nt / 32) *
+           (unsigned long long)v->r * (unsigned long long)v->nt * (unsigned long long)v->r;
 }
 
 Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,

@@ -103,11 +103,14 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
     Band bands[kMaxBins + 1];
     size_t n_bands = 0;
     for (int k = 0; k <= K; ++k) {
+        t->band[k][0] = t->band[k][1] = 0xFFFFFFFFu;
         if (t->c64[k] == 0.0) continue;
         Band b;
         guard_bounds(t->c64[k], &b.lo, &b.hi, nullptr);
         b.k = k;
         bands[n_bands++] = b;
+        t->band[k][0] = b.lo;
+        t->band[k][1] = b.hi;
     }
     // K >= 1 and the edges increase, so c_K > 0 and there is at least one band.
     t->h_top = bands[n_bands - 1].hi;

@@ -35,6 +35,7 @@ struct BinTable {
     int32_t n_lut;         // entries used
     int32_t n_complex;     // buckets holding more than one guard band
     double c64[kMaxBins + 1];            // FP64 squared-chord edges
+    uint32_t band[kMaxBins + 1][2];      // {lo_bits, hi_bits}: guard band of edge k (c_k > 0)
     uint32_t lut[kMaxLut][4];            // {lo_bits, hi_bits, slot_below, slot_above}
 };
 
@@ -135,6 +136,32 @@ PairParams make_params(const Variant* v, const BinTable& tab, const Segment* seg
                        unsigned long long* cursor, unsigned long long* stats);
 int launch_pairs(const Variant* v, const PairParams& prm, int grid, size_t smem, cudaStream_t st);
 int launch_finalize_segments(const Segment* d_segs, int n_segs, int K, cudaStream_t st);
+// Spatial order of n FP64 points (SoA, stride): *order = original indices
+// sorted by Hilbert key, or by (label, key) when labels (device, values in
+// [0, n_labels), n_labels <= 256) are given; *sorted_labels (optional) then
+// receives the labels in that order.  scratch: order_bytes(n, labels != 0).
+size_t order_bytes(long long n, int with_labels);
+int spatial_order(const double* x64, long long stride, long long n, int check,
+                  const int* labels, int n_labels, unsigned char* scratch, int sm_count,
+                  cudaStream_t st, const unsigned** order, const unsigned** sorted_labels);
+int launch_radec_to_xyz(const double* coords, long long n, double* xyz, int sm_count,
+                        cudaStream_t st);
+// sizes[l] += points with label l (sizes zeroed by the caller).
+int launch_count_labels(const unsigned* lab, long long n, int n_labels,
+                        unsigned long long* sizes, int sm_count, cudaStream_t st);
+// FP32 copies with region r's sorted points (positions src[r]..src[r+1]-1 of
+// order) from dst[r] on, sentinels up to dst[r+1]; dst[R] = n_pad.
+int launch_gather_regions(const double* x64, long long stride, const unsigned* order,
+                          const long long* src, const long long* dst, int R, long long n_pad,
+                          float4* p32, int tag, int sm_count, cudaStream_t st);
+// Bounding sphere of every chunk of 32 positions (sentinels mark padding).
+int launch_chunk_caps(const float4* p32, long long n_pad, float4* c32, int sm_count,
+                      cudaStream_t st);
+// Skipping over a table of counts: kept items per count, then each count's
+// kept range and list written into segs, their number into *n_kept.
+int launch_cull_batch(const CullSeg* cs, int n_segs, long long total, double theta_top,
+                      unsigned long long* kept, Segment* segs, unsigned long long* n_kept,
+                      int sm_count, cudaStream_t st);
 // Bounding cap of every tile of T points (real points [0, n)).
 int launch_tile_caps(const float4* p32, long long n, int T, long long tiles, TileCap* caps,
                      cudaStream_t st);

@@ -12,7 +12,8 @@
 //   - rounds: one persistent pair-count launch over a segment table drawn from
 //     every admitted, ready request: small requests first (up to half of a
 //     round), then the others in arrival order; a request that arrives while
-//     others are counting joins the next round instead of queueing behind them;
+//     others are counting joins the next round instead of queueing behind them
+//     (rounds double while the backlog is deep);
 //   - completion: after the round that holds a request's last tile pairs, the
 //     overflow slots and the copy of its counts to the host are queued on the
 //     same stream, so its counts are final when its event fires; w(theta) is
@@ -278,7 +279,11 @@ bool launch_round(wtheta_server* S, Round& R) {
     // behind large ones; the rest of the round goes to the others in arrival
     // order, each taking what it needs, so that a large request is delayed
     // only by earlier ones and by small ones.
-    long long budget = S->round_items;
+    // With a deep backlog, rounds twice as long: fewer launch tails; a
+    // request arriving meanwhile waits at most one such round.
+    long long backlog = 0;
+    for (Request* r : ready) backlog += remaining(r);
+    long long budget = backlog > 16 * S->round_items ? 2 * S->round_items : S->round_items;
     const long long small_items = S->round_items / 8;
     long long small_budget = budget / 2;
     std::vector<long long> give(ready.size(), 0);

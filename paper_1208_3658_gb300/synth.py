@@ -276,3 +276,15 @@ def serve_requests(seed: int = 1, n_requests: int = 2000, n_lo: int = 1_000,
             r2 = uniform(fp, n, seed, "serve", "random2", q)
             reqs.append(Request(float(t[q]), "cross", d, r, d2, r2))
     return reqs, (1.0 * ARCMIN, 10.0, 24)
+
+
+def grid_labels(ra_dec: np.ndarray, ra0: float, ra1: float, dec0: float, dec1: float,
+                nx: int, ny: int) -> np.ndarray:
+    """Region labels (int32) of points on an nx x ny grid of equal RA and Dec
+    steps over [ra0, ra1) x [dec0, dec1); points outside are clamped to the
+    nearest cell.  A jackknife region layout for patch footprints."""
+    rd = np.asarray(ra_dec, np.float64).reshape(-1, 2)
+    ra = np.mod(rd[:, 0] - ra0, 360.0)
+    ix = np.clip(np.floor(ra / (ra1 - ra0) * nx), 0, nx - 1).astype(np.int64)
+    iy = np.clip(np.floor((rd[:, 1] - dec0) / (dec1 - dec0) * ny), 0, ny - 1).astype(np.int64)
+    return (iy * nx + ix).astype(np.int32)

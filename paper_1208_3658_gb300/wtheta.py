@@ -100,6 +100,7 @@ def lib() -> ctypes.CDLL:
             vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
             i64, i32, u32p = ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(ctypes.c_uint32)
             u64p = ctypes.POINTER(ctypes.c_uint64)
+            i64p = ctypes.POINTER(ctypes.c_int64)
             L.wtheta_strerror.restype = ctypes.c_char_p
             L.wtheta_strerror.argtypes = [ctypes.c_int]
             L.wtheta_edges.argtypes = [ctypes.c_double, ctypes.c_double, i32, i32, dp]
@@ -114,6 +115,9 @@ def lib() -> ctypes.CDLL:
             L.wtheta_ls.argtypes = [u64p, u64p, u64p, i64, i64, i32, dp]
             L.wtheta_ls_cross.argtypes = [u64p, u64p, u64p, u64p, i64, i64, i64, i64, i32, dp]
             L.wtheta_estimate.argtypes = [u64p, u64p, u64p, i64, i64, i32, i32, dp]
+            L.wtheta_count_regions.argtypes = [vp, i64, vp, vp, i64, vp, i32, dp, i32, i32, vp,
+                                               i64p, vp]
+            L.wtheta_jackknife.argtypes = [u64p, i64p, i32, i32, dp, dp, dp]
             L.wtheta_correlate.argtypes = [dp, i64, dp, i64, dp, i32, u64p, dp, vp]
             L.wtheta_count_xyz_noalloc.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
             L.wtheta_batch_plan.argtypes = [ctypes.POINTER(wtheta_catalog_pair), i32, dp, i32,
@@ -475,6 +479,41 @@ def wtheta_estimate(DD, DR, RR, n_d: int, n_r: int, estimator: int) -> np.ndarra
     _check(lib().wtheta_estimate(p1, p2, p3, n_d, n_r, K, estimator, _host_f64(w)[1]),
            "wtheta_estimate")
     return w
+
+
+def wtheta_count_regions(coords_d, labels_d, coords_r, labels_r, edges, n_regions: int, counts,
+                         coords_are_xyz: bool = False, stream=None) -> np.ndarray:
+    """Region-pair DD, DR, RR into counts (device tensor, 3 x R x R x (K+2)
+    int64 viewed as uint64); returns the region sizes (2 x R int64)."""
+    e = np.ascontiguousarray(edges, np.float64)
+    K = len(e) - 1
+    per = 3 if coords_are_xyz else 2
+    n_d = _n_points(coords_d, per)
+    n_r = _n_points(coords_r, per)
+    sizes = np.zeros(2 * n_regions, np.int64)
+    _check(lib().wtheta_count_regions(_dev_ptr(coords_d), n_d, _dev_ptr(labels_d, 4, "labels_d"),
+                                      _dev_ptr(coords_r), n_r, _dev_ptr(labels_r, 4, "labels_r"),
+                                      1 if coords_are_xyz else 0, _host_f64(e)[1], K, n_regions,
+                                      _dev_ptr(counts),
+                                      sizes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      _stream(stream)),
+           "wtheta_count_regions")
+    return sizes
+
+
+def wtheta_jackknife(counts, sizes, n_regions: int):
+    """(w, w_jk, cov) from host region-pair counts and region sizes."""
+    c = np.ascontiguousarray(counts, np.uint64).reshape(-1)
+    sz = np.ascontiguousarray(sizes, np.int64)
+    K = c.size // (3 * n_regions * n_regions) - 2
+    w = np.empty(K, np.float64)
+    w_jk = np.empty((n_regions, K), np.float64)
+    cov = np.empty((K, K), np.float64)
+    _check(lib().wtheta_jackknife(c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                  sz.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n_regions, K,
+                                  _host_f64(w)[1], _host_f64(w_jk)[1], _host_f64(cov)[1]),
+           "wtheta_jackknife")
+    return w, w_jk, cov
 
 
 def wtheta_ls_cross(D1D2, D1R2, R1D2, R1R2, n_d1, n_d2, n_r1, n_r2) -> np.ndarray:

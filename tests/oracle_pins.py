@@ -157,6 +157,38 @@ def check_estimators_closed_forms():
     assert np.all(np.isnan(O.estimator(z, z, z, 10, 10, "hamilton")))
 
 
+def check_regions_and_jackknife():
+    """Region-pair counts sum to the whole counts; the jackknife sample k has
+    exactly the counts of the catalogues recounted without region k (the
+    definition of the sample), and its w is Eq. 2 of those; the covariance is
+    (R-1) times numpy's biased covariance of the samples."""
+    fp = synth.Patch(30.0, 6.0, -10.0, -4.0)
+    D = synth.clustered(fp, 700, 14, 3.0, 4, "test", "data")
+    Rn = synth.uniform(fp, 900, 4, "test", "random")
+    e = O.edges(1.0 * ARCMIN, 3.0, 10)
+    R = 6
+    ld = synth.grid_labels(D, 30.0, 36.0, -10.0, -4.0, 3, 2)
+    lr = synth.grid_labels(Rn, 30.0, 36.0, -10.0, -4.0, 3, 2)
+    XD, XR = O.radec_to_xyz(D), O.radec_to_xyz(Rn)
+    c = O.count_regions(XD, ld, XR, lr, e, R)
+    assert np.array_equal(c[0].sum(axis=(0, 1), dtype=np.uint64), O.count_xyz(XD, None, e, True))
+    assert np.array_equal(c[1].sum(axis=(0, 1), dtype=np.uint64), O.count_xyz(XD, XR, e, False))
+    assert np.array_equal(c[2].sum(axis=(0, 1), dtype=np.uint64), O.count_xyz(XR, None, e, True))
+    assert not c[0][np.tril_indices(R, -1)].any()
+    sizes = np.concatenate([np.bincount(ld, minlength=R), np.bincount(lr, minlength=R)])
+    w, w_k, cov = O.jackknife(c, sizes, R)
+    for k in (0, 3, 5):
+        Dk, Rk = XD[:, ld != k], XR[:, lr != k]
+        DD = O.count_xyz(np.ascontiguousarray(Dk), None, e, True)
+        DR = O.count_xyz(np.ascontiguousarray(Dk), np.ascontiguousarray(Rk), e, False)
+        RR = O.count_xyz(np.ascontiguousarray(Rk), None, e, True)
+        want = O.ls(DD, DR, RR, Dk.shape[1], Rk.shape[1])
+        assert np.array_equal(w_k[k], want, equal_nan=True)
+    ok = np.all(np.isfinite(w_k), axis=0)
+    ref = (R - 1) * np.cov(w_k[:, ok].T, bias=True)
+    assert np.allclose(cov[np.ix_(ok, ok)], ref, rtol=1e-12, atol=1e-15)
+
+
 def check_cross_identity():
     """Cross estimator with R1 = D1: d1d2 - d1r2 - r1d2 + r1r2 = 0."""
     e = O.edges(1.0 * ARCMIN, 5.0, 16)
@@ -235,6 +267,7 @@ def check_chord_values():
 
 ALL_CHECKS = [
     check_hand_placed, check_totals, check_dr_rd, check_d_equals_r,
-    check_r_is_d_twice, check_estimators_closed_forms, check_cross_identity, check_analytic_rr,
+    check_r_is_d_twice, check_estimators_closed_forms, check_regions_and_jackknife,
+    check_cross_identity, check_analytic_rr,
     check_bruteforce_angles, check_edges_modes, check_chord_values,
 ]

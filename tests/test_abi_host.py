@@ -232,3 +232,30 @@ def test_estimators_match_oracle(est, name):
         assert np.array_equal(got, W.wtheta_ls(DD, DR, RR, wl.n_d, wl.n_r), equal_nan=True)
     with pytest.raises(W.WthetaError):
         W.wtheta_estimate(DD, DR, RR, wl.n_d, wl.n_r, 4)
+
+
+def test_jackknife_matches_oracle():
+    """wtheta_jackknife on the oracle's region-pair counts equals the oracle's
+    jackknife (which sums the kept region pairs directly)."""
+    fp = synth.Patch(120.0, 8.0, 20.0, 28.0)
+    D = synth.clustered(fp, 900, 18, 3.0, 6, "test", "data")
+    Rn = synth.uniform(fp, 1100, 6, "test", "random")
+    e = O.edges(1.0 * ARCMIN, 4.0, 12)
+    R = 8
+    ld = synth.grid_labels(D, 120.0, 128.0, 20.0, 28.0, 4, 2)
+    lr = synth.grid_labels(Rn, 120.0, 128.0, 20.0, 28.0, 4, 2)
+    c = O.count_regions(O.radec_to_xyz(D), ld, O.radec_to_xyz(Rn), lr, e, R)
+    sizes = np.concatenate([np.bincount(ld, minlength=R), np.bincount(lr, minlength=R)])
+    w, w_k, cov = W.wtheta_jackknife(c, sizes, R)
+    w_o, w_ko, cov_o = O.jackknife(c, sizes, R)
+    scale = np.maximum(np.abs(w_o), 1.0)
+    ok = np.isfinite(w_o)
+    assert np.all(np.abs(w - w_o)[ok] <= 1e-12 * scale[ok])
+    okk = np.isfinite(w_ko)
+    assert np.array_equal(np.isfinite(w_k), okk)
+    assert np.all(np.abs(w_k - w_ko)[okk] <= 1e-12 * np.maximum(np.abs(w_ko[okk]), 1.0))
+    cols = np.all(okk, axis=0)
+    m = np.ix_(cols, cols)
+    assert np.allclose(cov[m], cov_o[m], rtol=1e-9, atol=1e-18)
+    with pytest.raises(W.WthetaError):
+        W.wtheta_jackknife(c[:, :1, :1], sizes[[0, R]], 1)
