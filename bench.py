@@ -148,6 +148,24 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def shared_atomic_roofline(W, sm_count, clk_mhz, st, pairs, tile):
+    """The histogram's roofline: measured shared reductions per SM per clock
+    (own word per thread, as the kernel's private columns; and one word for
+    all, the worst case), against the reductions the step issued at most: one
+    per pair binned through the table plus three per settled chunk and thread."""
+    private = W.wtheta_probe_shared_atomics(False)
+    same = W.wtheta_probe_shared_atomics(True)
+    binned = max(0.0, float(st[W.STAT_TILES]) * tile * tile - float(st[W.STAT_SPAN]))
+    reductions = binned + 3.0 * float(st[W.STAT_SPAN]) / 256.0   # thread-level
+    per_pair = reductions / max(1.0, float(pairs))
+    peak_lanes = sm_count * 32.0 * private * clk_mhz * 1e6      # thread reductions / s
+    return {"warp_reductions_per_sm_clock": {"own_word": private, "one_word": same},
+            "reductions_per_algorithmic_pair": per_pair,
+            "peak_algorithmic_pairs_per_s": peak_lanes / max(per_pair, 1e-30),
+            "note": "upper bound on the reductions: pairs of the kept tile pairs minus the "
+                    "pairs settled by span, plus 3 per settled chunk and thread"}
+
+
 def kernel_traffic():
     """DRAM bytes per launch of the pair kernel from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
@@ -313,6 +331,10 @@ def run_ours(args, rank, world, dist):
                            sm_count, FP32_LANES_PER_SM, clk, FP32_OPS_PER_PAIR, evaluated,
                            float(pairs))),
         "frac_at_max_clock": achieved / peak_max,
+        "shared_atomic": shared_atomic_roofline(
+            W, sm_count, clk, st, pairs,
+            (lambda t: t[0] * t[1])([int(x) for x in args.tune.split(",")]) if args.tune
+            else 1024),
         "kernel_ms_per_launch": {"DD": statistics.mean(r[0] for r in call_ms),
                                  "DR": statistics.mean(r[1] for r in call_ms),
                                  "RR": statistics.mean(r[2] for r in call_ms)},

@@ -474,6 +474,16 @@ int wtheta_jackknife(const uint64_t* counts, const int64_t* region_sizes, int32_
                      int32_t n_bins, double* w, double* w_jk, double* cov);
 
 /*
+ * Measurement: the shared-memory atomic throughput of the current device,
+ * for the pair kernel's second roofline (its histogram updates are shared
+ * reductions).  One block of 1024 threads per SM issues red.shared.add.u32,
+ * each thread to its own word (same_address = 0) or all to one word (1);
+ * *per_sm_per_clock receives warp-wide reductions per SM per SM clock.
+ * Synchronises the device.  Not part of the paper's method.
+ */
+int wtheta_probe_shared_atomics(int32_t same_address, double* per_sm_per_clock);
+
+/*
  * Whole w(theta) from host catalogues: copies data and randoms to the device
  * on stream, counts DD, DR, RR, copies the counts back and applies
  * wtheta_ls.  Synchronises stream before returning.

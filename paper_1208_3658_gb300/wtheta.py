@@ -118,6 +118,7 @@ def lib() -> ctypes.CDLL:
             L.wtheta_count_regions.argtypes = [vp, i64, vp, vp, i64, vp, i32, dp, i32, i32, vp,
                                                i64p, vp]
             L.wtheta_jackknife.argtypes = [u64p, i64p, i32, i32, dp, dp, dp]
+            L.wtheta_probe_shared_atomics.argtypes = [i32, dp]
             L.wtheta_correlate.argtypes = [dp, i64, dp, i64, dp, i32, u64p, dp, vp]
             L.wtheta_count_xyz_noalloc.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
             L.wtheta_batch_plan.argtypes = [ctypes.POINTER(wtheta_catalog_pair), i32, dp, i32,
@@ -514,6 +515,14 @@ def wtheta_jackknife(counts, sizes, n_regions: int):
                                   _host_f64(w)[1], _host_f64(w_jk)[1], _host_f64(cov)[1]),
            "wtheta_jackknife")
     return w, w_jk, cov
+
+
+def wtheta_probe_shared_atomics(same_address: bool) -> float:
+    """Warp-wide shared reductions per SM per clock on the current device."""
+    v = ctypes.c_double(0.0)
+    _check(lib().wtheta_probe_shared_atomics(1 if same_address else 0, ctypes.byref(v)),
+           "wtheta_probe_shared_atomics")
+    return float(v.value)
 
 
 def wtheta_ls_cross(D1D2, D1R2, R1D2, R1R2, n_d1, n_d2, n_r1, n_r2) -> np.ndarray:

@@ -373,3 +373,37 @@ def test_span_bins_near_an_edge(W):
     got = gpu_count_xyz(W, both, None, e, True, tune=dict(span_bins=1))
     want = O.count_xyz(both, None, e, True)
     assert np.array_equal(got, want)
+
+
+def test_span_bins_three_slots_near_two_edges(W):
+    """Group-chunk spans that cover two edges (three slots), with many pairs
+    inside both edges' guard bands: counts equal the oracle's bit for bit."""
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    k = 10
+    rng = np.random.default_rng(23)
+    n = 2500
+    ra = rng.uniform(-0.05, 0.05, n)
+    dec = rng.uniform(-0.05, 0.05, n)
+    A = synth.interleave(ra, dec)
+    mid = 0.5 * (e[k] + e[k + 1])
+    B = np.concatenate([synth.interleave(ra + e[k], dec), synth.interleave(ra + e[k + 1], dec),
+                        synth.interleave(rng.uniform(-0.05, 0.05, n) + mid,
+                                         rng.uniform(-0.05, 0.05, n))])
+    XA, XB = O.radec_to_xyz(A), O.radec_to_xyz(B)
+    st = torch.zeros(W.NSTATS, dtype=torch.int64, device="cuda")
+    got = gpu_count_xyz(W, XA, XB, e, False, tune=dict(span_bins=1), stats=st)
+    want = O.count_xyz(XA, XB, e, False)
+    assert np.array_equal(got, want)
+    st = st.cpu().numpy()
+    assert st[W.STAT_RECHECK] > 0 and st[W.STAT_SPAN] > 0
+    off = gpu_count_xyz(W, XA, XB, e, False, tune=dict(span_bins=2))
+    assert np.array_equal(off, want)
+
+
+def test_shared_atomic_probe(W):
+    """The measurement kernel returns a plausible rate: at most one warp-wide
+    reduction per SM clock per SM sub-partition, and fewer to one word."""
+    own = W.wtheta_probe_shared_atomics(False)
+    one = W.wtheta_probe_shared_atomics(True)
+    assert 0.01 < own <= 4.0
+    assert 0.0 < one <= own
