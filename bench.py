@@ -57,6 +57,9 @@ def parse_args():
                     help="threads,points_per_thread,hist_mode of the pair kernel (default: library's)")
     ap.add_argument("--no-skip-far", action="store_true",
                     help="evaluate every tile pair (no bounding-cap skipping): brute force")
+    ap.add_argument("--separate-counts", action="store_true",
+                    help="count DD, DR and RR with three wtheta_count calls (each catalogue "
+                         "prepared per call) instead of one wtheta_count_wtheta call")
     ap.add_argument("--no-span-bins", action="store_true",
                     help="bin every evaluated pair through the table (no per-chunk settling)")
     ap.add_argument("--n", type=int, default=0,
@@ -241,15 +244,27 @@ def run_ours(args, rank, world, dist):
     if args.no_span_bins:
         tune = dict(tune or {}, span_bins=2)
 
-    def step(evs=None):
+    n_calls = 3 if args.separate_counts else 1
+
+    def step(evs=None, stats=None):
+        if not args.separate_counts:
+            # one w(theta): both catalogues prepared once, DD, DR, RR in one launch
+            if evs is not None:
+                evs[0][0].record(stream)
+            W.wtheta_count_wtheta(d_data, d_rand, False, e, counts, tune=tune, stats=stats,
+                                  stream=stream)
+            if evs is not None:
+                evs[0][1].record(stream)
+            return
         calls = [(d_data, None, True), (d_data, d_rand, False), (d_rand, None, True)]
         for q, (a, b, auto) in enumerate(calls):
             if evs is not None:
                 evs[q][0].record(stream)
-            if tune is None:
+            if tune is None and stats is None:
                 W.wtheta_count(a, b, e, auto, counts[q], stream=stream)
             else:
-                W.wtheta_count_ex(a, b, False, e, auto, counts[q], tune=tune, stream=stream)
+                W.wtheta_count_ex(a, b, False, e, auto, counts[q], tune=tune, stats=stats,
+                                  stream=stream)
             if evs is not None:
                 evs[q][1].record(stream)
 
@@ -264,8 +279,8 @@ def run_ours(args, rank, world, dist):
         gpu_id = u if u.startswith("GPU-") else "GPU-" + u
     sampler = ClockSampler(gpu_id if world == 1 else None)
     sampler.start()
-    step_evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(3)]
-                for _ in range(args.steps)]
+    step_evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                 for _ in range(n_calls)] for _ in range(args.steps)]
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -281,7 +296,7 @@ def run_ours(args, rank, world, dist):
     launches = W.wtheta_kernel_launches() - launches0
     clocks = sampler.stop()
 
-    call_ms = [[step_evs[k][q][0].elapsed_time(step_evs[k][q][1]) for q in range(3)]
+    call_ms = [[step_evs[k][q][0].elapsed_time(step_evs[k][q][1]) for q in range(n_calls)]
                for k in range(args.steps)]
     step_ms = [sum(c) for c in call_ms]
     ms = sum(step_ms) / args.steps
@@ -299,9 +314,7 @@ def run_ours(args, rank, world, dist):
 
     # statistics of one untimed step: binned and rechecked fractions
     stats = torch.zeros(W.NSTATS, dtype=torch.int64, device=dev)
-    tmpc = torch.zeros(K + 2, dtype=torch.int64, device=dev)
-    for a, b, auto in [(d_data, None, True), (d_data, d_rand, False), (d_rand, None, True)]:
-        W.wtheta_count_ex(a, b, False, e, auto, tmpc, tune=tune, stats=stats)
+    step(stats=stats)
     torch.cuda.synchronize()
     st = stats.cpu().numpy()
 
@@ -335,9 +348,11 @@ def run_ours(args, rank, world, dist):
             W, sm_count, clk, st, pairs,
             (lambda t: t[0] * t[1])([int(x) for x in args.tune.split(",")]) if args.tune
             else 1024),
-        "kernel_ms_per_launch": {"DD": statistics.mean(r[0] for r in call_ms),
-                                 "DR": statistics.mean(r[1] for r in call_ms),
-                                 "RR": statistics.mean(r[2] for r in call_ms)},
+        "kernel_ms_per_launch": ({"DD": statistics.mean(r[0] for r in call_ms),
+                                  "DR": statistics.mean(r[1] for r in call_ms),
+                                  "RR": statistics.mean(r[2] for r in call_ms)}
+                                 if args.separate_counts else
+                                 {"DD+DR+RR": statistics.mean(r[0] for r in call_ms)}),
     }
 
     out = {
@@ -348,6 +363,8 @@ def run_ours(args, rank, world, dist):
                    "tune": args.tune or "library default",
                    "skip_far_tile_pairs": not args.no_skip_far,
                    "span_bins": not args.no_span_bins,
+                   "api": ("three wtheta_count calls" if args.separate_counts else
+                           "wtheta_count_wtheta (DD, DR, RR in one launch)"),
                    "pairs_per_step": pairs, "l2": "flushed between steps (512 MB write)",
                    "inputs": "resident in HBM (FP64 RA/Dec), converted inside each call",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

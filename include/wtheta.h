@@ -197,6 +197,20 @@ int wtheta_count_ex(const double* coords_a, int64_t n_a, const double* coords_b,
                     const wtheta_tune* tune, uint64_t* stats, void* stream);
 
 /*
+ * The three counts of one w(theta) -- DD, DR and RR of a data catalogue and
+ * its randoms -- in one call: each catalogue is converted and ordered once,
+ * and the three counts are one persistent launch (far tile pairs skipped per
+ * count).  Same inputs as wtheta_count_ex for each catalogue;
+ *   counts: device, 3 x (K+2) uint64 (DD, DR, RR), overwritten;
+ *   tune, stats: as wtheta_count_ex (stats added over the three counts).
+ * Equal, slot for slot, to three wtheta_count_ex calls.
+ */
+int wtheta_count_wtheta(const double* coords_d, int64_t n_d, const double* coords_r,
+                        int64_t n_r, int32_t coords_are_xyz, const double* bin_edges_deg,
+                        int32_t n_bins, uint64_t* counts, const wtheta_tune* tune,
+                        uint64_t* stats, void* stream);
+
+/*
  * Batched counts: the DD, DR and RR of many (data, randoms) catalogue pairs
  * sharing one edge set, in one persistent launch captured in a CUDA graph.
  * The paper's §4 motivates it: Monte-Carlo error estimates of w(theta) need

@@ -599,10 +599,12 @@ __global__ void k_cull_items(const TileCap* __restrict__ ca, const TileCap* __re
 // item's index within its count is appended to that count's list (in any
 // order), kept[seg] counting them.
 __global__ void k_cull_batch(const CullSeg* __restrict__ cs, int n_segs, long long total,
-                             double theta_top, unsigned long long* __restrict__ kept) {
+                             double theta_top, unsigned long long* __restrict__ kept,
+                             unsigned long long* __restrict__ stats) {
     const long long stride = (long long)gridDim.x * blockDim.x;
     const long long n_round = (total + 31) / 32 * 32;
     const int lane = threadIdx.x & 31;
+    unsigned long long skipped = 0;
     for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n_round; g += stride) {
         bool keep = false;
         int seg = -1;
@@ -618,6 +620,7 @@ __global__ void k_cull_batch(const CullSeg* __restrict__ cs, int n_segs, long lo
             long long I, J;
             item_to_tiles(local, cs[seg].ta, cs[seg].tb, cs[seg].is_auto, &I, &J);
             keep = caps_may_meet(cs[seg].ca[I], cs[seg].cb[J], theta_top);
+            skipped += keep ? 0 : 1;
         }
         const unsigned peers = __match_any_sync(0xffffffffu, keep ? seg : -1);
         const int leader = __ffs(peers) - 1;
@@ -625,6 +628,11 @@ __global__ void k_cull_batch(const CullSeg* __restrict__ cs, int n_segs, long lo
         if (keep && lane == leader) base = atomicAdd(kept + seg, (unsigned long long)__popc(peers));
         base = __shfl_sync(0xffffffffu, base, leader);
         if (keep) cs[seg].list[base + __popc(peers & ((1u << lane) - 1u))] = (unsigned)local;
+    }
+    if (stats) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) skipped += __shfl_xor_sync(0xffffffffu, skipped, o);
+        if (lane == 0 && skipped) atomicAdd(stats + WTHETA_STAT_SKIPPED, skipped);
     }
 }
 
@@ -1570,10 +1578,10 @@ int launch_chunk_caps(const float4* p32, long long n_pad, float4* c32, int sm_co
 
 int launch_cull_batch(const CullSeg* cs, int n_segs, long long total, double theta_top,
                       unsigned long long* kept, Segment* segs, unsigned long long* n_kept,
-                      int sm_count, cudaStream_t st) {
+                      int sm_count, cudaStream_t st, unsigned long long* stats) {
     if (n_segs <= 0) return WTHETA_OK;
-    k_cull_batch<<<launch_grid(std::max(total, 1LL), sm_count), 256, 0, st>>>(cs, n_segs, total,
-                                                                             theta_top, kept);
+    k_cull_batch<<<launch_grid(std::max(total, 1LL), sm_count), 256, 0, st>>>(
+        cs, n_segs, total, theta_top, kept, stats);
     k_cull_prefix<<<1, 32, 0, st>>>(segs, cs, kept, n_segs, n_kept);
     count_launch(2);
     return check_cuda(cudaGetLastError());
@@ -1743,6 +1751,131 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
         fe = cudaFreeAsync(cull_scratch, st);
         if (!rc) rc = check_cuda(fe);
     }
+    return rc;
+}
+
+// The three counts of one w(theta) (DD, DR, RR) in one persistent launch:
+// each catalogue is prepared once, far tile pairs of each count are skipped
+// on the device, and the counts are three segments of one work table, so
+// there is one launch tail instead of three.  counts: device, 3 x (K+2).
+static int count_wtheta_impl(const double* cd, long long nd, const double* cr, long long nr,
+                             int is_xyz, const double* edges, int K,
+                             unsigned long long* counts, const wtheta_tune* tune,
+                             unsigned long long* stats, cudaStream_t st) {
+    if (!counts || nd < 0 || nr < 0 || (nd > 0 && !cd) || (nr > 0 && !cr) ||
+        (is_xyz != 0 && is_xyz != 1))
+        return WTHETA_EINVAL;
+    if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
+                 tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
+                 tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0 ||
+                 tune->skip_far < 0 || tune->skip_far > 2 || tune->span_bins < 0 ||
+                 tune->span_bins > 2))
+        return WTHETA_EINVAL;
+    static thread_local BinTable tab;
+    int rc = build_table(edges, K, &tab);
+    if (rc) return rc;
+    DeviceInfo di;
+    if ((rc = device_info(&di))) return rc;
+    const size_t K2 = (size_t)K + 2;
+    if ((rc = check_cuda(cudaMemsetAsync(counts, 0, 3 * K2 * 8, st)))) return rc;
+    const Variant* v = pick_variant(tune, K, tab.n_lut, di.max_smem_optin);
+    if (!v) return WTHETA_EINVAL;
+    const long long T = (long long)v->nt * v->r;
+    const long long pd = round_up(nd, T), pr = round_up(nr, T);
+    const long long td = pd / T, tr = pr / T;
+    const unsigned long long ndd = (unsigned long long)nd * (unsigned long long)(nd > 0 ? nd - 1 : 0) / 2;
+    const unsigned long long ndr = (unsigned long long)nd * (unsigned long long)nr;
+    const unsigned long long nrr = (unsigned long long)nr * (unsigned long long)(nr > 0 ? nr - 1 : 0) / 2;
+    // the counts with work, biggest first
+    struct Cnt { int kind; long long items; unsigned long long total; };
+    Cnt all[3] = {{0, td * (td + 1) / 2, ndd}, {1, td * tr, ndr}, {2, tr * (tr + 1) / 2, nrr}};
+    std::vector<Cnt> cnts;
+    for (const Cnt& c : all)
+        if (c.total > 0) cnts.push_back(c);
+    std::stable_sort(cnts.begin(), cnts.end(),
+                     [](const Cnt& a, const Cnt& b) { return a.items > b.items; });
+    const int n_segs = (int)cnts.size();
+    long long total_items = 0;
+    for (const Cnt& c : cnts) total_items += c.items;
+    const bool cull = (!tune || tune->skip_far != 2) && edges[K] < 180.0 && td * td < (1LL << 32) &&
+                      td * tr < (1LL << 32) && tr * tr < (1LL << 32);
+    // scratch: cursor and kept total, segments, culling table, kept counts,
+    // both prepared catalogues, tile caps, kept lists
+    const size_t ba = prepare_bytes(nd, pd, is_xyz), bb = prepare_bytes(nr, pr, is_xyz);
+    size_t bytes = 256 + 1024 + 1024 + 256;
+    const size_t off_d = bytes;
+    bytes += (ba + 255) / 256 * 256;
+    const size_t off_r = bytes;
+    bytes += (bb + 255) / 256 * 256;
+    const size_t off_caps = bytes;
+    if (cull) bytes += ((size_t)(td + tr) * sizeof(TileCap) + 255) / 256 * 256;
+    const size_t off_lists = bytes;
+    if (cull) bytes += (size_t)total_items * 4;
+    unsigned char* m = nullptr;
+    if ((rc = check_cuda(cudaMallocAsync((void**)&m, bytes, st)))) return rc;
+    unsigned long long* cursor = (unsigned long long*)m;
+    unsigned long long* n_kept = cursor + 1;
+    Segment* d_segs = (Segment*)(m + 256);
+    CullSeg* d_cull = (CullSeg*)(m + 256 + 1024);
+    unsigned long long* d_kept = (unsigned long long*)(m + 256 + 2048);
+    static_assert(3 * sizeof(Segment) <= 1024 && 3 * sizeof(CullSeg) <= 1024, "tables fit");
+    Prepared D, R;
+    rc = prepare(cd, nd, pd, is_xyz, 0, m + off_d, di.sm_count, st, &D);
+    if (!rc) rc = prepare(cr, nr, pr, is_xyz, 1, m + off_r, di.sm_count, st, &R);
+    TileCap* caps_d = (TileCap*)(m + off_caps);
+    TileCap* caps_r = caps_d + td;
+    if (!rc && cull) {
+        rc = launch_tile_caps(D.p32, nd, (int)T, td, caps_d, st);
+        if (!rc) rc = launch_tile_caps(R.p32, nr, (int)T, tr, caps_r, st);
+    }
+    Segment segs[3];
+    CullSeg cs[3];
+    long long item = 0;
+    for (int i = 0; i < n_segs; ++i) {
+        const int k = cnts[i].kind;
+        const Prepared& A = k == 2 ? R : D;
+        const Prepared& B = k == 0 ? D : R;
+        const long long ta = k == 2 ? tr : td, tb = k == 0 ? td : tr;
+        segs[i] = make_segment(A, B, ta, tb, k != 1, item, counts + (size_t)k * K2, cnts[i].total);
+        std::memset(&cs[i], 0, sizeof(CullSeg));
+        cs[i].begin = item;
+        cs[i].n = cnts[i].items;
+        cs[i].ta = ta;
+        cs[i].tb = tb;
+        cs[i].is_auto = k != 1;
+        cs[i].ca = k == 2 ? caps_r : caps_d;
+        cs[i].cb = k == 0 ? caps_d : caps_r;
+        cs[i].list = (unsigned*)(m + off_lists) + item;
+        item += cnts[i].items;
+    }
+    if (!rc && n_segs > 0) {
+        rc = check_cuda(cudaMemcpyAsync(d_segs, segs, sizeof(Segment) * n_segs,
+                                        cudaMemcpyHostToDevice, st));
+        if (!rc) rc = check_cuda(cudaMemsetAsync(m, 0, 16, st));
+        if (!rc && cull) {
+            rc = check_cuda(cudaMemcpyAsync(d_cull, cs, sizeof(CullSeg) * n_segs,
+                                            cudaMemcpyHostToDevice, st));
+            if (!rc) rc = check_cuda(cudaMemsetAsync(d_kept, 0, 3 * 8, st));
+            if (!rc)
+                rc = launch_cull_batch(d_cull, n_segs, total_items,
+                                       edges[K] * (3.14159265358979323846 / 180.0), d_kept,
+                                       d_segs, n_kept, di.sm_count, st, stats);
+        }
+        const size_t smem = v->smem(K, tab.n_lut);
+        int grid = 0;
+        const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
+        if (!rc) rc = grid_for(v, smem, total_items, di.sm_count, want_per_sm, &grid);
+        if (!rc) {
+            PairParams prm = make_params(v, tab, nullptr, d_segs, n_segs, 0, total_items, cursor,
+                                         stats);
+            if (cull) prm.n_items_dev = n_kept;
+            prm.span = !(tune && tune->span_bins == 2);
+            rc = launch_pairs(v, prm, grid, smem, st);
+        }
+        if (!rc) rc = launch_finalize_segments(d_segs, n_segs, K, st);
+    }
+    const cudaError_t fe = cudaFreeAsync(m, st);
+    if (!rc) rc = check_cuda(fe);
     return rc;
 }
 
@@ -2151,7 +2284,7 @@ static int plan_capture(wtheta_plan* P, const DeviceInfo& di) {
             if (!rc) rc = check_cuda(cudaMemsetAsync(P->d_kept, 0, (size_t)P->n_segs * 8, cs));
             if (!rc) {
                 k_cull_batch<<<launch_grid(P->total_items, di.sm_count), 256, 0, cs>>>(
-                    P->d_cull, P->n_segs, P->total_items, P->theta_top, P->d_kept);
+                    P->d_cull, P->n_segs, P->total_items, P->theta_top, P->d_kept, nullptr);
                 k_cull_prefix<<<1, 32, 0, cs>>>(P->d_segs, P->d_cull, P->d_kept, P->n_segs,
                                                 P->d_total);
                 count_launch(2);
@@ -2438,6 +2571,15 @@ int wtheta_get_error(void* stream, uint32_t* code) {
     return WTHETA_OK;
 }
 
+int wtheta_count_wtheta(const double* coords_d, int64_t n_d, const double* coords_r,
+                        int64_t n_r, int32_t coords_are_xyz, const double* bin_edges_deg,
+                        int32_t n_bins, uint64_t* counts, const wtheta_tune* tune,
+                        uint64_t* stats, void* stream) {
+    return count_wtheta_impl(coords_d, n_d, coords_r, n_r, coords_are_xyz, bin_edges_deg, n_bins,
+                             (unsigned long long*)counts, tune, (unsigned long long*)stats,
+                             (cudaStream_t)stream);
+}
+
 int wtheta_correlate(const double* data, int64_t n_d, const double* rand, int64_t n_r,
                      const double* edges, int32_t K, uint64_t* counts_out, double* w_out,
                      void* stream) {
@@ -2455,9 +2597,7 @@ int wtheta_correlate(const double* data, int64_t n_d, const double* rand, int64_
     double* dr = dd + 2 * n_d;
     rc = check_cuda(cudaMemcpyAsync(dd, data, (size_t)n_d * 16, cudaMemcpyHostToDevice, st));
     if (!rc) rc = check_cuda(cudaMemcpyAsync(dr, rand, (size_t)n_r * 16, cudaMemcpyHostToDevice, st));
-    if (!rc) rc = count_impl(dd, n_d, nullptr, 0, 0, edges, K, 1, dc, nullptr, nullptr, st);
-    if (!rc) rc = count_impl(dd, n_d, dr, n_r, 0, edges, K, 0, dc + nslot, nullptr, nullptr, st);
-    if (!rc) rc = count_impl(dr, n_r, nullptr, 0, 0, edges, K, 1, dc + 2 * nslot, nullptr, nullptr, st);
+    if (!rc) rc = count_wtheta_impl(dd, n_d, dr, n_r, 0, edges, K, dc, nullptr, nullptr, st);
     uint64_t host_counts[3 * (kMaxBins + 2)];
     if (!rc)
         rc = check_cuda(cudaMemcpyAsync(host_counts, dc, 3 * nslot * 8, cudaMemcpyDeviceToHost, st));

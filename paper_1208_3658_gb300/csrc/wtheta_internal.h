@@ -161,7 +161,7 @@ int launch_chunk_caps(const float4* p32, long long n_pad, float4* c32, int sm_co
 // kept range and list written into segs, their number into *n_kept.
 int launch_cull_batch(const CullSeg* cs, int n_segs, long long total, double theta_top,
                       unsigned long long* kept, Segment* segs, unsigned long long* n_kept,
-                      int sm_count, cudaStream_t st);
+                      int sm_count, cudaStream_t st, unsigned long long* stats = nullptr);
 // Bounding cap of every tile of T points (real points [0, n)).
 int launch_tile_caps(const float4* p32, long long n, int T, long long tiles, TileCap* caps,
                      cudaStream_t st);

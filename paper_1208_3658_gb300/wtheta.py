@@ -121,6 +121,8 @@ def lib() -> ctypes.CDLL:
             L.wtheta_probe_shared_atomics.argtypes = [i32, dp]
             L.wtheta_correlate.argtypes = [dp, i64, dp, i64, dp, i32, u64p, dp, vp]
             L.wtheta_count_xyz_noalloc.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
+            L.wtheta_count_wtheta.argtypes = [vp, i64, vp, i64, i32, dp, i32, vp,
+                                              ctypes.POINTER(wtheta_tune), vp, vp]
             L.wtheta_batch_plan.argtypes = [ctypes.POINTER(wtheta_catalog_pair), i32, dp, i32,
                                             ctypes.POINTER(wtheta_tune), vp,
                                             ctypes.POINTER(ctypes.c_void_p)]
@@ -447,6 +449,20 @@ def wtheta_count_ex(coords_a, coords_b, coords_are_xyz: bool, edges_deg, is_auto
                                  1 if coords_are_xyz else 0, ep, len(e) - 1, 1 if is_auto else 0,
                                  _dev_ptr(counts), ctypes.byref(t) if t is not None else None,
                                  _dev_ptr(stats), _stream(stream)), "wtheta_count_ex")
+
+
+def wtheta_count_wtheta(coords_d, coords_r, coords_are_xyz: bool, edges_deg, counts,
+                        tune: dict | None = None, stats=None, stream=None):
+    """DD, DR, RR of one w(theta) into counts (device, 3 x (K+2) int64 viewed
+    as uint64), in one persistent launch."""
+    e, ep = _host_f64(edges_deg)
+    per = 3 if coords_are_xyz else 2
+    t = _tune_struct(tune)
+    _check(lib().wtheta_count_wtheta(_dev_ptr(coords_d), _n_points(coords_d, per),
+                                     _dev_ptr(coords_r), _n_points(coords_r, per),
+                                     1 if coords_are_xyz else 0, ep, len(e) - 1, _dev_ptr(counts),
+                                     ctypes.byref(t) if t is not None else None, _dev_ptr(stats),
+                                     _stream(stream)), "wtheta_count_wtheta")
 
 
 def wtheta_radec_to_xyz(ra_dec, xyz, stream=None):

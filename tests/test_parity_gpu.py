@@ -407,3 +407,40 @@ def test_shared_atomic_probe(W):
     one = W.wtheta_probe_shared_atomics(True)
     assert 0.01 < own <= 4.0
     assert 0.0 < one <= own
+
+
+@pytest.mark.parametrize("case", ["small", "survey_200k", "tiny", "empty_rand"])
+def test_count_wtheta_equals_three_counts(W, case):
+    """DD, DR, RR in one launch (each catalogue prepared once) equal the three
+    single counts, slot for slot, and the statistics add up."""
+    if case == "small":
+        wl = synth.small()
+        d, r = wl.data, wl.rand
+    elif case == "survey_200k":
+        wl = synth.survey(n=200_000)
+        d, r = wl.data, wl.rand
+    elif case == "tiny":
+        wl = synth.small(n=1500)
+        d, r = wl.data[:14], wl.rand[:2 * 1100]   # 7 data points, 1100 randoms
+    else:
+        wl = synth.small(n=1500)
+        d, r = wl.data, wl.rand[:0]
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    K = len(e) - 1
+    dd, rr = dev(d), dev(r)
+    one = torch.zeros((3, K + 2), dtype=torch.int64, device="cuda")
+    st1 = torch.zeros(W.NSTATS, dtype=torch.int64, device="cuda")
+    W.wtheta_count_wtheta(dd, rr, False, e, one, stats=st1)
+    three = torch.zeros_like(one)
+    st3 = torch.zeros_like(st1)
+    for q, (a, b, auto) in enumerate([(dd, None, True), (dd, rr, False), (rr, None, True)]):
+        W.wtheta_count_ex(a, b, False, e, auto, three[q], stats=st3)
+    torch.cuda.synchronize()
+    assert torch.equal(one, three), case
+    s1, s3 = st1.cpu().numpy(), st3.cpu().numpy()
+    assert s1[W.STAT_TILES] == s3[W.STAT_TILES] and s1[W.STAT_SKIPPED] == s3[W.STAT_SKIPPED]
+    if case == "small":
+        want = O.wtheta(d, r, e)[:3]
+        got = one.cpu().numpy().astype(np.uint64)
+        for k in range(3):
+            assert int(got[k].sum()) == int(want[k].sum())
