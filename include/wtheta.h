@@ -488,6 +488,14 @@ int wtheta_jackknife(const uint64_t* counts, const int64_t* region_sizes, int32_
                      int32_t n_bins, double* w, double* w_jk, double* cov);
 
 /*
+ * Fault injection on the host, for tests of the failure paths: the device
+ * allocation made after `after` more successful ones fails with
+ * WTHETA_ENOMEM (after = 0: the next one); -1 turns it off.  No GPU work is
+ * involved in the failure.  Process-wide.
+ */
+int wtheta_inject_alloc_failure(int32_t after);
+
+/*
  * Measurement: the shared-memory atomic throughput of the current device,
  * for the pair kernel's second roofline (its histogram updates are shared
  * reductions).  One block of 1024 threads per SM issues red.shared.add.u32,

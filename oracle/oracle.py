@@ -10,7 +10,10 @@ paper's statement of the problem and by mathematics: points at constructed
 separations, pair totals (Sec. 2), DR = RD, the exact w = 2/n when the random
 catalogue equals the data (Eq. 2 with the pair totals), the analytic pair
 fraction for uniform full-sky randoms, and an independent long-double
-angle-space evaluation of App. A's formula on small inputs.
+angle-space evaluation of App. A's formula on small inputs; the other
+estimators by their closed forms when the randoms are the data (once or
+twice over); the region-pair counts by their sums and the jackknife samples
+by recounting the catalogues without each region.
 """
 from __future__ import annotations
 

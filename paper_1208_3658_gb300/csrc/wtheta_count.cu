@@ -32,6 +32,7 @@
 //   - counts go to private per-thread (or per-warp, warp-aggregated) uint32
 //     shared histograms, flushed into uint64 global counts before any can wrap.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -1512,6 +1513,7 @@ size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
 
 int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int tag,
                    unsigned char* scratch, int sm_count, cudaStream_t st, Prepared* out) {
+    TraceRange trace("prepare");
     unsigned char* sp = scratch;
     float4* p32 = (float4*)sp;
     sp += ((size_t)n_pad * 16 + 255) / 256 * 256;
@@ -1638,6 +1640,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
                       int is_xyz, const double* edges, int K, int is_auto,
                       unsigned long long* counts, const wtheta_tune* tune,
                       unsigned long long* stats, cudaStream_t st) {
+    TraceRange trace("wtheta_count");
     if (!counts || n_a < 0 || n_b < 0 || (is_auto != 0 && is_auto != 1) ||
         (is_xyz != 0 && is_xyz != 1))
         return WTHETA_EINVAL;
@@ -1684,7 +1687,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     const size_t bb = is_auto ? 0 : prepare_bytes(n_b, pb, is_xyz);
     void* scratch = nullptr;
     void* cull_scratch = nullptr;
-    if ((rc = check_cuda(cudaMallocAsync(&scratch, 256 + ba + bb, st)))) return rc;
+    if ((rc = dev_malloc_async(&scratch, 256 + ba + bb, st))) return rc;
     unsigned char* sp = (unsigned char*)scratch;
     unsigned long long* cursor = (unsigned long long*)sp;
     Prepared A, B;
@@ -1703,7 +1706,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     if (!rc && skip_far) {
         const size_t cull_bytes = 256 + (size_t)(ta + tb) * sizeof(TileCap) + (size_t)n_items * 4;
         void* cs = nullptr;
-        rc = check_cuda(cudaMallocAsync(&cs, cull_bytes, st));
+        rc = dev_malloc_async(&cs, cull_bytes, st);
         if (!rc) {
             cull_scratch = cs;
             n_list = (unsigned long long*)cs;
@@ -1762,6 +1765,7 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
                              int is_xyz, const double* edges, int K,
                              unsigned long long* counts, const wtheta_tune* tune,
                              unsigned long long* stats, cudaStream_t st) {
+    TraceRange trace("wtheta_count_wtheta");
     if (!counts || nd < 0 || nr < 0 || (nd > 0 && !cd) || (nr > 0 && !cr) ||
         (is_xyz != 0 && is_xyz != 1))
         return WTHETA_EINVAL;
@@ -1812,7 +1816,7 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     const size_t off_lists = bytes;
     if (cull) bytes += (size_t)total_items * 4;
     unsigned char* m = nullptr;
-    if ((rc = check_cuda(cudaMallocAsync((void**)&m, bytes, st)))) return rc;
+    if ((rc = dev_malloc_async((void**)&m, bytes, st))) return rc;
     unsigned long long* cursor = (unsigned long long*)m;
     unsigned long long* n_kept = cursor + 1;
     Segment* d_segs = (Segment*)(m + 256);
@@ -1912,6 +1916,40 @@ int launch_cull_items(const TileCap* ca, const TileCap* cb, long long ta, long l
 }
 
 void add_launches(long long n) { g_launches.fetch_add((unsigned long long)n); }
+
+// -1: no injected failure; n >= 0: the allocation after n more succeed fails
+static std::atomic<long long> g_fail_alloc{-1};
+
+static bool injected_failure() {
+    long long v = g_fail_alloc.load();
+    while (v >= 0) {
+        if (g_fail_alloc.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
+}
+
+int dev_malloc(void** p, size_t bytes) {
+    if (injected_failure()) return WTHETA_ENOMEM;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return WTHETA_ENOMEM;
+    }
+    return check_cuda(e);
+}
+
+int dev_malloc_async(void** p, size_t bytes, cudaStream_t st) {
+    if (injected_failure()) return WTHETA_ENOMEM;
+    const cudaError_t e = cudaMallocAsync(p, bytes, st);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return WTHETA_ENOMEM;
+    }
+    return check_cuda(e);
+}
+
+TraceRange::TraceRange(const char* name) { nvtxRangePushA(name); }
+TraceRange::~TraceRange() { nvtxRangePop(); }
 
 // ---------------------------------------------------------------------------
 // allocation-free variant of the xyz count
@@ -2100,7 +2138,7 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
     }
     if (P->scratch) cudaFree(P->scratch);
     P->scratch = nullptr;
-    int rc = check_cuda(cudaMalloc(&P->scratch, bytes));
+    int rc = dev_malloc(&P->scratch, bytes);
     if (rc) return rc;
     unsigned char* base = (unsigned char*)P->scratch;
     P->d_cursor = (unsigned long long*)base;
@@ -2160,7 +2198,7 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
     if (P->cull_mem) cudaFree(P->cull_mem);
     P->cull_mem = nullptr;
     P->caps.assign(2 * nc, nullptr);
-    if ((rc = check_cuda(cudaMalloc(&P->d_segs, sizeof(Segment) * sorted.size())))) return rc;
+    if ((rc = dev_malloc((void**)&P->d_segs, sizeof(Segment) * sorted.size()))) return rc;
     if (P->cull) {
         // kept counters, total, the count table, every catalogue's tile caps,
         // and one list of item indices per count
@@ -2174,7 +2212,7 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
         }
         const size_t off_lists = cb;
         cb += (size_t)items * 4;
-        if ((rc = check_cuda(cudaMalloc(&P->cull_mem, cb)))) return rc;
+        if ((rc = dev_malloc(&P->cull_mem, cb))) return rc;
         unsigned char* cm = (unsigned char*)P->cull_mem;
         P->d_kept = (unsigned long long*)cm;
         P->d_total = P->d_kept + P->n_segs;
@@ -2363,8 +2401,8 @@ static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, const do
     if (!rc) rc = device_info(&di);
     if (!rc) rc = check_cuda(cudaGetDevice(&P->dev));
     if (!rc)
-        rc = check_cuda(cudaMalloc(&P->d_counts, (size_t)n_cats * 3 * (K + 2) * sizeof(unsigned long long)));
-    if (!rc) rc = check_cuda(cudaMalloc(&P->d_stats, 8 * WTHETA_NSTATS));
+        rc = dev_malloc((void**)&P->d_counts, (size_t)n_cats * 3 * (K + 2) * sizeof(unsigned long long));
+    if (!rc) rc = dev_malloc((void**)&P->d_stats, 8 * WTHETA_NSTATS);
     if (rc) {
         plan_release(P);
         return rc;
@@ -2480,6 +2518,7 @@ int wtheta_batch_plan(const wtheta_catalog_pair* cats, int32_t n_cats, const dou
 
 int wtheta_batch_run(wtheta_plan* P, uint64_t* counts, void* stream) {
     if (!P || !counts) return WTHETA_EINVAL;
+    TraceRange trace("wtheta_batch_run");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return WTHETA_ECUDA;
     if (dev != P->dev) return WTHETA_EINVAL;
@@ -2544,7 +2583,7 @@ int wtheta_count_shard(const double* a, int64_t n_a, const double* b, int64_t n_
                     nullptr, nullptr, st);
     if (rc || r1 >= n_a || r1 == r0) return rc;
     unsigned long long* tmp = nullptr;
-    if ((rc = check_cuda(cudaMallocAsync(&tmp, sizeof(unsigned long long) * (K + 2), st))))
+    if ((rc = dev_malloc_async((void**)&tmp, sizeof(unsigned long long) * (K + 2), st)))
         return rc;
     rc = count_impl(rows, r1 - r0, a + 2 * r1, n_a - r1, 0, edges, K, 0, tmp, nullptr, nullptr,
                     st);
@@ -2571,6 +2610,12 @@ int wtheta_get_error(void* stream, uint32_t* code) {
     return WTHETA_OK;
 }
 
+int wtheta_inject_alloc_failure(int32_t after) {
+    if (after < -1) return WTHETA_EINVAL;
+    g_fail_alloc.store(after);
+    return WTHETA_OK;
+}
+
 int wtheta_count_wtheta(const double* coords_d, int64_t n_d, const double* coords_r,
                         int64_t n_r, int32_t coords_are_xyz, const double* bin_edges_deg,
                         int32_t n_bins, uint64_t* counts, const wtheta_tune* tune,
@@ -2591,7 +2636,7 @@ int wtheta_correlate(const double* data, int64_t n_d, const double* rand, int64_
     const size_t nslot = (size_t)K + 2;
     void* buf = nullptr;
     const size_t bytes = 256 + (size_t)(n_d + n_r) * 16 + 3 * nslot * 8;
-    if ((rc = check_cuda(cudaMallocAsync(&buf, bytes, st)))) return rc;
+    if ((rc = dev_malloc_async(&buf, bytes, st))) return rc;
     unsigned long long* dc = (unsigned long long*)buf;  // 3 (K+2) counts
     double* dd = (double*)((unsigned char*)buf + ((3 * nslot * 8 + 255) / 256) * 256);
     double* dr = dd + 2 * n_d;

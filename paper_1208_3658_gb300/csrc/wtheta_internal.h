@@ -172,6 +172,21 @@ int launch_cull_items(const TileCap* ca, const TileCap* cb, long long ta, long l
                       unsigned long long* n_list, int sm_count, cudaStream_t st);
 void add_launches(long long n);
 
+// Device allocations of the library go through these, so that a test can make
+// the n-th one fail on the host (wtheta_inject_alloc_failure) without
+// touching the GPU.  Both return WTHETA_OK, WTHETA_ENOMEM or WTHETA_ECUDA.
+int dev_malloc(void** p, size_t bytes);
+int dev_malloc_async(void** p, size_t bytes, cudaStream_t st);
+
+// A named range on the host timeline (NVTX), for profilers; costs nothing
+// measurable when no tool is attached.
+struct TraceRange {
+    explicit TraceRange(const char* name);
+    ~TraceRange();
+    TraceRange(const TraceRange&) = delete;
+    TraceRange& operator=(const TraceRange&) = delete;
+};
+
 // Host-side helpers (wtheta_host.cpp).
 int validate_edges(const double* edges_deg, int K);
 void chord2_edges(const double* edges_deg, int K, double* c);

@@ -52,6 +52,7 @@ int count_regions_impl(const double* cd, long long nd, const int* ld, const doub
                        long long nr, const int* lr, int is_xyz, const double* edges, int K,
                        int R, unsigned long long* counts, long long* sizes_out,
                        cudaStream_t st) {
+    TraceRange trace("wtheta_count_regions");
     if (!counts || !sizes_out || nd < 0 || nr < 0 || R < 1 || R > 256 ||
         (nd > 0 && (!cd || !ld)) || (nr > 0 && (!cr || !lr)))
         return WTHETA_EINVAL;
@@ -80,7 +81,7 @@ int count_regions_impl(const double* cd, long long nd, const int* ld, const doub
         b1 += order_bytes(n_of[c], 1);
     }
     unsigned char* m1 = nullptr;
-    if ((rc = check_cuda(cudaMallocAsync((void**)&m1, b1, st)))) return rc;
+    if ((rc = dev_malloc_async((void**)&m1, b1, st))) return rc;
     unsigned long long* d_sizes = (unsigned long long*)(m1 + 256);
     const double* x64[2];
     const unsigned* order[2] = {nullptr, nullptr};
@@ -159,7 +160,7 @@ int count_regions_impl(const double* cd, long long nd, const int* ld, const doub
     const size_t off_lists = b2;
     b2 += (size_t)total_items * 4;
     unsigned char* m2 = nullptr;
-    if ((rc = check_cuda(cudaMallocAsync((void**)&m2, b2, st)))) {
+    if ((rc = dev_malloc_async((void**)&m2, b2, st))) {
         cudaFreeAsync(m1, st);
         return rc;
     }

@@ -164,8 +164,9 @@ void free_host(Request* r) {
 // Admission: device memory from the stream-ordered pool on the upload
 // stream, copies in, conversion and spatial ordering, counts zeroed.
 int admit(wtheta_server* S, Request* r) {
+    TraceRange trace("server_admit");
     const long long T = (long long)S->v->nt * S->v->r;
-    int rc = check_cuda(cudaMallocAsync(&r->dmem, r->dev_bytes, S->up));
+    int rc = dev_malloc_async(&r->dmem, r->dev_bytes, S->up);
     if (rc) return rc;
     unsigned char* p = (unsigned char*)r->dmem;
     r->d_counts = (unsigned long long*)p;
@@ -264,6 +265,7 @@ long long remaining(const Request* r) {
 // Builds and launches one round on the compute stream; returns true if it
 // launched one.  Called with the server lock held.
 bool launch_round(wtheta_server* S, Round& R) {
+    TraceRange trace("server_round");
     std::vector<Request*> ready;
     for (Request* r : S->active)
         if (r->state == kCounting && remaining(r) > 0) {
@@ -386,6 +388,10 @@ void worker_loop(wtheta_server* S) {
             r->t_admit = now_s(S);
             const int rc = admit(S, r);
             if (rc) {
+                if (r->dmem) {
+                    cudaFreeAsync(r->dmem, S->up);
+                    r->dmem = nullptr;
+                }
                 r->state = kFailed;
                 r->status = rc;
                 r->t_done = now_s(S);
@@ -456,9 +462,9 @@ int server_create(const double* edges, int K, size_t budget, int max_active,
     for (Round& R : S->rounds) {
         if (rc) break;
         R.cap = 4096;
-        rc = check_cuda(cudaMalloc(&R.d_segs, sizeof(Segment) * R.cap));
+        rc = dev_malloc((void**)&R.d_segs, sizeof(Segment) * R.cap);
         if (!rc) rc = check_cuda(cudaMallocHost(&R.h_segs, sizeof(Segment) * R.cap));
-        if (!rc) rc = check_cuda(cudaMalloc(&R.d_cursor, 8));
+        if (!rc) rc = dev_malloc((void**)&R.d_cursor, 8);
         if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&R.done, cudaEventDisableTiming));
     }
     if (rc) {

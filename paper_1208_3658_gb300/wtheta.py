@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
                                                i64p, vp]
             L.wtheta_jackknife.argtypes = [u64p, i64p, i32, i32, dp, dp, dp]
             L.wtheta_probe_shared_atomics.argtypes = [i32, dp]
+            L.wtheta_inject_alloc_failure.argtypes = [i32]
             L.wtheta_correlate.argtypes = [dp, i64, dp, i64, dp, i32, u64p, dp, vp]
             L.wtheta_count_xyz_noalloc.argtypes = [vp, i64, vp, i64, dp, i32, i32, vp, vp]
             L.wtheta_count_wtheta.argtypes = [vp, i64, vp, i64, i32, dp, i32, vp,
@@ -531,6 +532,12 @@ def wtheta_jackknife(counts, sizes, n_regions: int):
                                   _host_f64(w)[1], _host_f64(w_jk)[1], _host_f64(cov)[1]),
            "wtheta_jackknife")
     return w, w_jk, cov
+
+
+def wtheta_inject_alloc_failure(after: int):
+    """The device allocation after `after` more successful ones fails
+    (host-side injection); -1 turns it off."""
+    _check(lib().wtheta_inject_alloc_failure(int(after)), "wtheta_inject_alloc_failure")
 
 
 def wtheta_probe_shared_atomics(same_address: bool) -> float:
