@@ -169,6 +169,15 @@ def shared_atomic_roofline(W, sm_count, clk_mhz, st, pairs, tile):
                     "pairs settled by span, plus 3 per settled chunk and thread"}
 
 
+def kernel_code_sha():
+    """Hash of the device code of the pair kernel's source file: the text from
+    the namespace opening to the host launch code (so host-only edits keep a
+    measurement valid, any kernel edit voids it)."""
+    t = open(KERNEL_SOURCE, "rb").read()
+    start = t.index(b"namespace wtheta {")
+    return hashlib.sha256(t[start:t.index(b"// launch plumbing")]).hexdigest()[:16]
+
+
 def kernel_traffic():
     """DRAM bytes per launch of the pair kernel from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
@@ -176,8 +185,8 @@ def kernel_traffic():
         text = open(PROFILE_SUMMARY).read()
     except OSError:
         return None
-    src = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()[:16]
-    m_sha = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    src = kernel_code_sha()
+    m_sha = re.search(r"kernel_code_sha256_16:\s*([0-9a-f]+)", text)
     m_tr = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", text)
     if not m_sha or not m_tr or m_sha.group(1) != src:
         return None
