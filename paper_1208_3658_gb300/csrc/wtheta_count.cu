@@ -1364,6 +1364,7 @@ const Variant* variants(int* n) {
         make_variant<128, 8, 1, kHistLaneAtomic, 1>(), make_variant<64, 16, 2, kHistLaneAtomic, 1>(),
         make_variant<64, 16, 2, kHistWarp, 0>(),       make_variant<128, 16, 2, kHistLaneAtomic, 1>(),
         make_variant<256, 8, 2, kHistLaneAtomic, 1>(), make_variant<256, 8, 2, kHistWarp, 0>(),
+        make_variant<64, 8, 2, kHistLaneAtomic, 0>(),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;
@@ -1390,6 +1391,21 @@ int device_info(DeviceInfo* out) {
     }
     *out = cache[dev];
     return WTHETA_OK;
+}
+
+// The default shape for one call: tiles of 512 points (64 threads) when the
+// larger catalogue has at most 64k points, so that a small count still has
+// tile pairs for every SM; the 1024-point shape otherwise.
+const Variant* pick_for_size(const wtheta_tune* tune, long long n_max, int K, int n_lut,
+                             int max_smem) {
+    if (!tune && n_max <= 65536) {
+        wtheta_tune small = {};
+        small.threads = 64;
+        small.points_per_thread = 8;
+        const Variant* v = pick_variant(&small, K, n_lut, max_smem);
+        if (v) return v;
+    }
+    return pick_variant(tune, K, n_lut, max_smem);
 }
 
 const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, int max_smem) {
@@ -1677,7 +1693,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
         return check_cuda(cudaGetLastError());
     }
 
-    const Variant* v = pick_variant(tune, K, tab.n_lut, di.max_smem_optin);
+    const Variant* v = pick_for_size(tune, std::max(n_a, n_b), K, tab.n_lut, di.max_smem_optin);
     if (!v) return WTHETA_EINVAL;  // no instantiated shape matches the tuning request
     const long long T = (long long)v->nt * v->r;  // TA == TB
     const long long pa = round_up(n_a, T), pb = is_auto ? pa : round_up(n_b, T);
@@ -1782,7 +1798,7 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     if ((rc = device_info(&di))) return rc;
     const size_t K2 = (size_t)K + 2;
     if ((rc = check_cuda(cudaMemsetAsync(counts, 0, 3 * K2 * 8, st)))) return rc;
-    const Variant* v = pick_variant(tune, K, tab.n_lut, di.max_smem_optin);
+    const Variant* v = pick_for_size(tune, std::max(nd, nr), K, tab.n_lut, di.max_smem_optin);
     if (!v) return WTHETA_EINVAL;
     const long long T = (long long)v->nt * v->r;
     const long long pd = round_up(nd, T), pr = round_up(nr, T);

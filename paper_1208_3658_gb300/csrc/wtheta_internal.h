@@ -120,6 +120,8 @@ struct Prepared {
 int device_info(DeviceInfo* out);
 const Variant* variants(int* n);
 const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, int max_smem);
+const Variant* pick_for_size(const wtheta_tune* tune, long long n_max, int K, int n_lut,
+                             int max_smem);
 int grid_for(const Variant* v, size_t smem, long long n_items, int sm_count, int want_per_sm,
              int* grid);
 long long round_up(long long x, long long m);
