@@ -55,6 +55,8 @@ extern "C" {
 #define WTHETA_EBUDGET (-5)  /* a request does not fit the memory budget     */
 #define WTHETA_EDEVICE (-6)  /* the device error word is non-zero            */
 #define WTHETA_ESIZE (-7)    /* input larger than a fixed-capacity entry point takes */
+#define WTHETA_EBUSY (-8)    /* the object is in a state that forbids the call */
+#define WTHETA_ECANCELED (-9) /* the request was cancelled before it ran      */
 
 /* bits of the device error word (wtheta_get_error) */
 #define WTHETA_DERR_NONFINITE 1u  /* an input coordinate is NaN or infinite  */
@@ -348,6 +350,12 @@ int wtheta_server_wait(wtheta_server* server, uint64_t req_id, int64_t timeout_m
                        uint64_t* counts, double* w);
 
 int wtheta_server_request_info(wtheta_server* server, uint64_t req_id, wtheta_request_info* info);
+
+/* Cancels a request that is still queued (not yet admitted): it ends in
+ * state WTHETA_RS_FAILED with status WTHETA_ECANCELED, and its wait returns
+ * that status.  WTHETA_EBUSY once it has been admitted (its work is on the
+ * device and runs to the end). */
+int wtheta_server_cancel(wtheta_server* server, uint64_t req_id);
 
 /* Forgets a finished request (frees its host copies). */
 int wtheta_server_release(wtheta_server* server, uint64_t req_id);

@@ -196,6 +196,9 @@ const char* wtheta_strerror(int status) {
         case WTHETA_ETIMEOUT: return "bounded wait timed out";
         case WTHETA_EBUDGET: return "request exceeds the memory budget";
         case WTHETA_EDEVICE: return "device reported invalid input";
+        case WTHETA_ESIZE: return "input larger than the entry point takes";
+        case WTHETA_EBUSY: return "not in a state that allows the call";
+        case WTHETA_ECANCELED: return "request cancelled";
         default: return "unknown status";
     }
 }

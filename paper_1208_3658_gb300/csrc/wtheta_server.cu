@@ -572,6 +572,23 @@ int wtheta_server_request_info(wtheta_server* S, uint64_t id, wtheta_request_inf
     return WTHETA_OK;
 }
 
+int wtheta_server_cancel(wtheta_server* S, uint64_t id) {
+    if (!S) return WTHETA_EINVAL;
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->all.find(id);
+    if (it == S->all.end()) return WTHETA_EINVAL;
+    Request* r = it->second;
+    if (r->state != kQueued) return WTHETA_EBUSY;  // admitted: its work is on the device
+    auto q = std::find(S->queue.begin(), S->queue.end(), r);
+    if (q != S->queue.end()) S->queue.erase(q);
+    r->state = kFailed;
+    r->status = WTHETA_ECANCELED;
+    r->t_done = now_s(S);
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+    return WTHETA_OK;
+}
+
 int wtheta_server_release(wtheta_server* S, uint64_t id) {
     if (!S) return WTHETA_EINVAL;
     std::lock_guard<std::mutex> g(S->mu);

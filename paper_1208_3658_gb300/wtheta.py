@@ -21,6 +21,7 @@ HEADER = os.path.join(os.path.dirname(_PKG), "include", "wtheta.h")
 
 WTHETA_OK = 0
 STATUS = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ETIMEOUT", -5: "EBUDGET",
+          -8: "EBUSY", -9: "ECANCELED",
           -6: "EDEVICE", -7: "ESIZE"}
 NOALLOC_MAX_POINTS, NOALLOC_TILE = 262144, 1024
 BINS_LINEAR, BINS_LN, BINS_LOG10 = 0, 1, 2
@@ -140,6 +141,7 @@ def lib() -> ctypes.CDLL:
             L.wtheta_server_request_info.argtypes = [vp, ctypes.c_uint64,
                                                      ctypes.POINTER(wtheta_request_info)]
             L.wtheta_server_release.argtypes = [vp, ctypes.c_uint64]
+            L.wtheta_server_cancel.argtypes = [vp, ctypes.c_uint64]
             L.wtheta_server_stats.argtypes = [vp, ctypes.POINTER(wtheta_server_stats_t)]
             L.wtheta_server_destroy.argtypes = [vp]
             L.wtheta_shard_rows.argtypes = [i64, i64, i32, i32, i32,
@@ -421,6 +423,10 @@ def wtheta_server_request_info(srv: Server, req_id: int) -> dict:
     _check(lib().wtheta_server_request_info(srv.handle, req_id, ctypes.byref(info)),
            "wtheta_server_request_info")
     return {k: getattr(info, k) for k, _ in wtheta_request_info._fields_}
+
+
+def wtheta_server_cancel(srv: Server, req_id: int):
+    _check(lib().wtheta_server_cancel(srv.handle, req_id), "wtheta_server_cancel")
 
 
 def wtheta_server_release(srv: Server, req_id: int):

@@ -76,3 +76,39 @@ def test_server_request_fails_alone(W):
     finally:
         W.wtheta_inject_alloc_failure(-1)
         W.wtheta_server_destroy(srv)
+
+
+def test_server_cancel_queued_request(W):
+    """A request cancelled while it waits for admission ends WTHETA_ECANCELED
+    and never runs; one already admitted cannot be cancelled (WTHETA_EBUSY);
+    the others complete exactly."""
+    e = W.wtheta_edges(1.0 / 60.0, 4.0, 16)
+    fp = synth.Patch(80.0, 8.0, -20.0, -12.0)
+    big = (synth.clustered(fp, 500_000, 10_000, 3.0, 7, "test", "data"),
+           synth.uniform(fp, 500_000, 7, "test", "random"))
+    small = [(synth.clustered(fp, 2000 + 300 * q, 40, 3.0, 8 + q, "test", "data"),
+              synth.uniform(fp, 2100 + 300 * q, 8 + q, "test", "random")) for q in range(3)]
+    # one admitted request at a time: the small ones wait in the queue
+    srv = W.wtheta_server_create(e, 8 << 30, max_active=1)
+    try:
+        i_big = W.wtheta_server_submit(srv, *big)
+        ids = [W.wtheta_server_submit(srv, *m) for m in small]
+        assert W.wtheta_server_request_info(srv, ids[1])["state"] == W.RS_QUEUED
+        W.wtheta_server_cancel(srv, ids[1])
+        with pytest.raises(W.WthetaError) as ex:
+            W.wtheta_server_wait(srv, ids[1], timeout_ms=60_000)
+        assert ex.value.status == -9
+        assert W.wtheta_server_request_info(srv, ids[1])["state"] == W.RS_FAILED
+        done, _, _ = W.wtheta_server_wait(srv, i_big, timeout_ms=120_000)
+        assert done
+        with pytest.raises(W.WthetaError) as ex:
+            W.wtheta_server_cancel(srv, i_big)
+        assert ex.value.status == -8
+        for q in (0, 2):
+            done, c, _ = W.wtheta_server_wait(srv, ids[q], timeout_ms=120_000)
+            assert done
+            want = O.wtheta(small[q][0], small[q][1], e)[:3]
+            for k in range(3):
+                assert np.array_equal(c[k], want[k])
+    finally:
+        W.wtheta_server_destroy(srv)
