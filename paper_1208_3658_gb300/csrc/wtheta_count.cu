@@ -946,10 +946,16 @@ __device__ __forceinline__ void three_slot_step(unsigned bxy_base, unsigned bz_b
     }
 }
 
-// One step of a two-slot chunk: the squared chords of JU B points with the
-// thread's R A points, computed exactly as in chords(), then d = s - mid.
-// neg[q] counts the values with d < 0 and mb[q] keeps the smallest |d|, one
-// accumulator per A pair q so that the steps' dependency chains interleave.
+// One step of a two-slot chunk: for JU B points and the thread's R A points,
+// d = s - mid evaluated as fma(dz, dz, fma(dy, dy, fma(dx, dx, -mid))) from the
+// same FP32 differences as chords().  Each fma rounds once, on a magnitude of
+// at most max(s, mid), so for s <= 2c + 1e-12 (the only values near the edge)
+// |d - (s - mid)| stays within the three roundings the guard band already
+// allows for s (gamma_3 (s + E1), evaluated at 2c + 1e-12), and |d| > G
+// settles the side of the FP64 squared chord exactly as the band does; far
+// above the edge d is large and positive.  neg[q] counts the values with
+// d < 0 and mb[q] keeps the smallest |d|, one accumulator per A pair q so that
+// the steps' dependency chains interleave.
 template <int R, int JU>
 __device__ __forceinline__ void two_slot_step(unsigned bxy_base, unsigned bz_base,
                                               const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
@@ -965,9 +971,8 @@ __device__ __forceinline__ void two_slot_step(unsigned bxy_base, unsigned bz_bas
             const f2_t dx = add2(ax[q], bx);
             const f2_t dy = add2(ay[q], by);
             const f2_t dz = add2(az[q], bz);
-            const f2_t t = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
             float d0, d1;
-            unpack2(add2(t, nmid), d0, d1);
+            unpack2(fma2(dz, dz, fma2(dy, dy, fma2(dx, dx, nmid))), d0, d1);
             mb[q] = min3f(mb[q], fabsf(d0), fabsf(d1));
             neg[q] += (__float_as_uint(d0) >> 31) + (__float_as_uint(d1) >> 31);
         }

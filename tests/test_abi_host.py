@@ -259,3 +259,46 @@ def test_jackknife_matches_oracle():
     assert np.allclose(cov[m], cov_o[m], rtol=1e-9, atol=1e-18)
     with pytest.raises(W.WthetaError):
         W.wtheta_jackknife(c[:, :1, :1], sizes[[0, R]], 1)
+
+
+def _emulate_fused_d(A, B, mid):
+    """The two-slot chunk's d = fma(dz, dz, fma(dy, dy, fma(dx, dx, -mid))),
+    each fma emulated as an FP64 sum rounded to FP32 (dx^2 is exact in FP64;
+    where the FP64 sum itself rounds, the emulation can differ from a true fma
+    by one FP32 ulp, which the band's factor-2 margin covers)."""
+    a = A.astype(np.float32)
+    b = B.astype(np.float32)
+    d = a - b
+    f64 = np.float64
+    x1 = (d[0].astype(f64) ** 2 - f64(mid)).astype(np.float32)
+    x2 = (d[1].astype(f64) ** 2 + x1.astype(f64)).astype(np.float32)
+    return (d[2].astype(f64) ** 2 + x2.astype(f64)).astype(np.float32)
+
+
+@pytest.mark.parametrize("lo,hi,K,mode", EDGE_SETS)
+def test_fused_edge_difference_classifies_exactly(lo, hi, K, mode):
+    """The two-slot chunks compare d = s - mid, with the subtraction fused
+    into the squared chord; outside |d| <= G (G the half-width of the edge's
+    guard band about its middle mid) the sign of d must give the side of the
+    FP64 squared chord, for pairs placed around every edge."""
+    rng = np.random.default_rng(999 + K)
+    e = W.wtheta_edges(lo, hi, K, mode)
+    c = W.wtheta_chord2_edges(e)
+    lo_b, hi_b, _ = W.wtheta_guard_band(e)
+    decided = 0
+    for k in range(K + 1):
+        if e[k] == 0.0:
+            continue
+        lo_f = np.array([lo_b[k]], np.uint32).view(np.float32)[0]
+        hi_f = np.array([hi_b[k]], np.uint32).view(np.float32)[0]
+        mid = np.float32(np.float32(0.5) * (lo_f + hi_f))
+        G = max(np.float32(mid - lo_f), np.float32(hi_f - mid))
+        rel = np.concatenate([-np.logspace(-12, -1, 500), np.logspace(-12, -1, 500)])
+        theta = np.clip(e[k] * (1 + rel), 1e-9, 180.0)
+        A, B = _pairs_at(theta, rng)
+        d = _emulate_fused_d(A, B, mid)
+        s64 = _s64(A, B)
+        out = np.abs(d) > G
+        assert np.all((d[out] > 0) == (s64[out] >= c[k])), k
+        decided += int(out.sum())
+    assert decided > 0
