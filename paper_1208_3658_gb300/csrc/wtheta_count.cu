@@ -108,6 +108,24 @@ __device__ __forceinline__ uint4 lds_u4(unsigned a) {
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
     return v;
 }
+__device__ __forceinline__ double lds_f64(unsigned a) {
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ long long lds_s64(unsigned a) {
+    long long v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ unsigned lds_u32(unsigned a) {
+    unsigned v;
+    asm volatile("ld.shared.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void sts_u32(unsigned a, unsigned v) {
+    asm volatile("st.shared.b32 [%0], %1;" :: "r"(a), "r"(v) : "memory");
+}
 __device__ __forceinline__ void red_add_shared(unsigned a, unsigned v) {
     asm volatile("red.shared.add.u32 [%0], %1;" :: "r"(a), "r"(v) : "memory");
 }
@@ -655,9 +673,10 @@ __global__ void k_cull_prefix(Segment* __restrict__ segs, const CullSeg* __restr
 
 // FP64 recheck: the definition's squared chord and slot for the pair of
 // sorted positions (ia, jb), found in the caller's FP64 arrays through the
-// original indices kept in the FP32 copies.
+// original indices kept in the FP32 copies; c64 is the shared address of
+// the FP64 edges.
 __device__ __forceinline__ unsigned recheck_slot(const Segment& S, long long ia, long long jb,
-                                                 const double* __restrict__ c64, int K) {
+                                                 unsigned c64, int K) {
     const long long i = __float_as_int(S.a32[ia].w);
     const long long j = __float_as_int(S.b32[jb].w);
     const double* a = S.a64;
@@ -668,7 +687,7 @@ __device__ __forceinline__ unsigned recheck_slot(const Segment& S, long long ia,
     const double dz = __dsub_rn(a[2 * as + i], b[2 * bs + j]);
     const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     unsigned k = 0;
-    while (k <= (unsigned)K && c64[k] <= s) ++k;
+    while (k <= (unsigned)K && lds_f64(c64 + 8u * k) <= s) ++k;
     return k;  // K+1 = overflow
 }
 
@@ -749,13 +768,13 @@ __device__ __forceinline__ bool bin_values(const float (&s)[NV], unsigned col, u
 // Rare: the step held values inside a guard band.  Given the step's values
 // again, take back their provisional counts and add each to the row its FP64
 // recheck gives (one copy of the recheck code, in a loop over a bitmask).
-template <int NT, int R, int NV, int HM>
+template <int NT, int R, int NV, int HM, typename Cnt>
 __device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsigned col, unsigned lut,
                                                  int shift, int base, int top_idx,
                                                  unsigned row_bytes, int K, const Segment& S,
                                                  long long a0, long long bj,
-                                                 const double* __restrict__ sC,
-                                                 unsigned long long& n_recheck) {
+                                                 unsigned sC,
+                                                 Cnt& n_recheck) {
     unsigned mask = 0;
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
@@ -820,7 +839,7 @@ __device__ __forceinline__ float min_of(const float (&s)[NV]) {
 // binned through the table (values inside a guard band settled in FP64).
 template <int NT, int R, int JU, int HM, bool DIAG>
 __device__ __forceinline__ void exact_steps(int j0, int j1, unsigned bxy, unsigned bz,
-                                            unsigned lut, const double* __restrict__ sC,
+                                            unsigned lut, unsigned sC,
                                             unsigned col, const f2_t (&ax)[R / 2],
                                             const f2_t (&ay)[R / 2], const f2_t (&az)[R / 2],
                                             float hf, int shift, int base, int top_idx,
@@ -878,17 +897,14 @@ __device__ __forceinline__ float4 group_cap(const f2_t (&ax)[R / 2], const f2_t 
 // classifies both ends (values inside a guard band or a bucket with several
 // edges are ambiguous):
 //   0  both ends in one slot: every pair is in slot rlo;
-//   1  adjacent slots k and k+1, split by edge k alone (its guard band
-//      [x, y] from the band table at shared address band): each pair is in
-//      rlo or rhi by one FP32 comparison, outside the band;
-//   3  slots k, k+1, k+2, split by edges k (edge) and k+1 (edge2): two
-//      comparisons per pair;
+//   1  adjacent slots k and k+1 (rlo = slot k), split by edge k alone: each
+//      pair is in one or the other by one FP32 comparison outside the
+//      edge's guard band;
+//   3  slots k, k+1, k+2, split by edges k and k+1: two comparisons per pair;
 //   2  anything else: bin pair by pair.
-// Rows are byte offsets of slots, slot << row_shift.
-__device__ __forceinline__ int span_mode(float4 ga, float4 gb, unsigned lut, int shift, int base,
-                                         int top_idx, unsigned band, int row_shift,
-                                         unsigned& rlo, unsigned& rhi, uint2& edge,
-                                         uint2& edge2) {
+// rlo is a byte offset of a slot's row, slot << row_shift.
+__device__ __forceinline__ int span_class(float4 ga, float4 gb, unsigned lut, int shift, int base,
+                                          int top_idx, int row_shift, unsigned& rlo) {
     const float dx = ga.x - gb.x, dy = ga.y - gb.y, dz = ga.z - gb.z;
     const float dc = sqrtf(dx * dx + dy * dy + dz * dz);
     const float rr = (ga.w + gb.w) * (1.f + 1e-6f) + 1e-6f;
@@ -901,18 +917,10 @@ __device__ __forceinline__ int span_mode(float4 ga, float4 gb, unsigned lut, int
     const uint4 eh = lut_entry(bh, lut, shift, base, top_idx);
     if (!(bl < el.x || bl > el.y) || !(bh < eh.x || bh > eh.y)) return 2;
     rlo = bl < el.x ? el.z : el.w;
-    rhi = bh < eh.x ? eh.z : eh.w;
+    const unsigned rhi = bh < eh.x ? eh.z : eh.w;
     if (rlo == rhi) return 0;
-    if (rhi == rlo + (1u << row_shift) || rhi == rlo + (2u << row_shift)) {
-        const unsigned a = band + 8u * (rlo >> row_shift);
-        unsigned lo, hi;
-        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(a));
-        edge = make_uint2(lo, hi);
-        if (rhi == rlo + (1u << row_shift)) return 1;
-        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(a + 8u));
-        edge2 = make_uint2(lo, hi);
-        return 3;
-    }
+    if (rhi == rlo + (1u << row_shift)) return 1;
+    if (rhi == rlo + (2u << row_shift)) return 3;
     return 2;
 }
 
@@ -982,16 +990,13 @@ __device__ __forceinline__ void two_slot_step(unsigned bxy_base, unsigned bz_bas
 // The pairs of the thread's R A points (tile positions a_first ..) with the
 // B points [j_begin, j_end) of the staged tile.
 template <int NT, int R, int JU, int HM, int DEF, bool DIAG>
-__device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lut, unsigned caps,
-                                          unsigned band, const double* __restrict__ sC,
-                                          unsigned hist,
+__device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lut,
+                                          unsigned sC, unsigned hist,
                                           const f2_t (&ax)[R / 2], const f2_t (&ay)[R / 2],
-                                          const f2_t (&az)[R / 2], const float4& ga,
-                                          const PairParams& p, const Segment& S, long long I,
-                                          long long J, int a_first, int j_begin, int j_end,
-                                          unsigned long long& n_recheck,
-                                          unsigned long long& n_span,
-                                          unsigned long long& n_skip) {
+                                          const f2_t (&az)[R / 2], const PairParams& p,
+                                          const Segment& S, long long I, long long J, int a_first,
+                                          int j_begin, int j_end,
+                                          unsigned long long& n_recheck) {
     using PK = PairKernel<NT, R, JU, HM, DEF>;
     constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
     constexpr int NV = JU * R;
@@ -1060,75 +1065,146 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
         }
         return;
     }
-    if (DIAG || !p.span || !S.b_caps) {
-        exact_steps<NT, R, JU, HM, DIAG>(j_begin, j_end, bxy, bz, lut, sC, col, ax, ay, az, hf,
-                                         shift, base, top_idx, row_bytes, K, S, a0, b0, a_first,
-                                         n_recheck);
-        return;
+    // pair by pair (diagonal tiles, or span binning off; spans go through
+    // span_item's jobs)
+    exact_steps<NT, R, JU, HM, DIAG>(j_begin, j_end, bxy, bz, lut, sC, col, ax, ay, az, hf, shift,
+                                     base, top_idx, row_bytes, K, S, a0, b0, a_first, n_recheck);
+}
+
+// The thread's R A points, R consecutive points of the spatial order (a
+// compact group: see span_class), packed two by two for the FP32x2
+// instructions.  Each value goes through an explicit add of +0 (exact; it
+// only turns -0 into +0, which leaves every squared chord unchanged): the
+// packed operands then get registers of their own instead of being formed in
+// place from the vector-load destinations, a layout measured to cost about a
+// quarter of the screening loop's throughput.
+template <int R>
+__device__ __forceinline__ void load_group(const float4* __restrict__ gA, f2_t (&ax)[R / 2],
+                                           f2_t (&ay)[R / 2], f2_t (&az)[R / 2]) {
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) {
+        const float4 a = gA[2 * q];
+        const float4 b = gA[2 * q + 1];
+        ax[q] = pack2(__fadd_rn(a.x, 0.f), __fadd_rn(b.x, 0.f));
+        ay[q] = pack2(__fadd_rn(a.y, 0.f), __fadd_rn(b.y, 0.f));
+        az[q] = pack2(__fadd_rn(a.z, 0.f), __fadd_rn(b.z, 0.f));
     }
-    // Chunks of 32 B points: the warp bins a chunk pair by pair only if one
-    // of its threads has to; otherwise each thread settles its A points
-    // against the chunk in one slot or with one comparison per pair.
-    constexpr int CH = 32;
-    static_assert(TB % (4 * CH) == 0 && CH % JU == 0, "whole chunks");
+}
+
+// ---------------------------------------------------------------------------
+// Span jobs.  A (group, chunk) pair whose span needs its pairs computed (two
+// slots, three slots, or pair by pair) is a job: the lane whose R A points
+// form the group, its sub-tile, the chunk's index in the staged B tile and
+// the lowest slot of the span.  Each warp keeps one ring of 32 jobs per kind
+// in shared memory and runs a full ring as one round, one job per lane: a
+// lane computes only pairs whose slot is not known from the spheres, whatever
+// its own group's spans, and the lanes of a round run the same loop.  A job's
+// A points are read again from the FP32 copy of the catalogue (L2).
+// ---------------------------------------------------------------------------
+constexpr int kJobTwo = 0, kJobThree = 1, kJobExact = 2, kJobKinds = 3, kChunk = 32;
+
+__device__ __forceinline__ unsigned job_word(int lane, int sub, int chunk, unsigned slot) {
+    return (unsigned)lane | ((unsigned)sub << 5) | ((unsigned)chunk << 8) | (slot << 16);
+}
+
+// Chunk c of the B tile starts its steps at point JU c (mod 32): lanes of a
+// round on neighbouring chunks then read points in different banks.
+template <int JU>
+__device__ __forceinline__ int chunk_point(int c0, int t, int rot) {
+    return c0 + ((t + rot) & (kChunk - 1));
+}
+
+__device__ __forceinline__ unsigned atom_add_shared(unsigned a, unsigned v) {
+    unsigned old;
+    asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(a), "r"(v) : "memory");
+    return old;
+}
+
+// A chunk's pairs with the lane's R A points (tile positions a_first ..)
+// binned pair by pair through the table, values inside a guard band settled
+// in FP64.  The tile pair (I, J) is read from shared memory (sIJ) only for
+// those.
+template <int NT, int R, int JU, int HM>
+__device__ __forceinline__ void exact_chunk(int c0, int rot, int a_first, unsigned sIJ,
+                                            unsigned bxy, unsigned bz, unsigned lut, unsigned sC,
+                                            unsigned col, const f2_t (&ax)[R / 2],
+                                            const f2_t (&ay)[R / 2], const f2_t (&az)[R / 2],
+                                            const PairParams& p, const Segment& S,
+                                            unsigned& n_recheck) {
+    using PK = PairKernel<NT, R, JU, HM, 0>;
+    constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
+    constexpr int NV = R;  // one B point per step: fewer live values
+    const float hf = __uint_as_float(p.tab.h_top);
+    const int shift = p.tab.shift, base = p.tab.base, top_idx = p.tab.n_lut - 1;
 #pragma unroll 1
-    for (int c0 = j_begin; c0 < j_end; c0 += CH) {
-        const uint4 gbu = lds_u4(caps + 16u * (unsigned)(c0 / CH));
-        const float4 gb = make_float4(__uint_as_float(gbu.x), __uint_as_float(gbu.y),
-                                      __uint_as_float(gbu.z), __uint_as_float(gbu.w));
-        unsigned rlo = 0, rhi = 0;
-        uint2 edge = make_uint2(0u, 0u), edge2 = make_uint2(0x7f800000u, 0x7f800000u);
-        const int mode = span_mode(ga, gb, lut, shift, base, top_idx, band, row_shift, rlo, rhi,
-                                   edge, edge2);
-        if (__any_sync(0xffffffffu, mode == 2)) {
-            exact_steps<NT, R, JU, HM, false>(c0, c0 + CH, bxy, bz, lut, sC, col, ax, ay, az, hf,
-                                              shift, base, top_idx, row_bytes, K, S, a0, b0,
-                                              a_first, n_recheck);
-            continue;
+    for (int t = 0; t < kChunk; ++t) {
+        const int j = chunk_point<JU>(c0, t, rot);
+        float s[NV];
+        chords<NT, R, 1, false>(s, bxy, bz, ax, ay, az, j, 0);
+        if (!(min_of(s) <= hf)) continue;
+        if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx)) {
+            float s2[NV];
+            chords<NT, R, 1, false>(s2, bxy, bz, ax, ay, az, j, 0);
+            const long long a0 = lds_s64(sIJ) * TA + a_first;
+            const long long b0 = lds_s64(sIJ + 8u) * TB;
+            recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, HCOLS * 4u,
+                                               p.tab.K, S, a0, b0 + j, sC, n_recheck);
         }
-        if (mode == 0) {
-            hist_add<HM>(col + rlo, (unsigned)(R * CH));
-            n_span += R * CH;
-        }
-        if (__all_sync(0xffffffffu, mode == 0)) {
-            n_skip += R * CH;
-            continue;
-        }
-        // Two slots: d = s - mid with mid the middle of the edge's guard band
-        // [lo, hi] and G its half-width (both exact: the band is narrow).
-        // |d| > G puts s outside the band, and then d < 0 means below it.
-        const float lo_f = __uint_as_float(edge.x), hi_f = __uint_as_float(edge.y);
-        const float mid = 0.5f * (lo_f + hi_f);
-        const float G = fmaxf(mid - lo_f, hi_f - mid);
-        const f2_t nmid = pack2(-mid, -mid);
-        if (__any_sync(0xffffffffu, mode == 3)) {
-            // Three slots for some thread: a second edge (+inf for the others,
-            // whose second count is then zero).
-            const float lo2 = __uint_as_float(edge2.x), hi2 = __uint_as_float(edge2.y);
-            const float mid2 = 0.5f * (lo2 + hi2);
-            const float G2 = fmaxf(mid2 - lo2, hi2 - mid2);
-            unsigned neg1 = 0, neg2 = 0;
-            float mb1 = __int_as_float(0x7f800000), mb2 = __int_as_float(0x7f800000);
-#pragma unroll 2
-            for (int j = c0; j < c0 + CH; j += JU)
-                three_slot_step<R, JU>(bxy, bz, ax, ay, az, j, nmid, pack2(-mid2, -mid2), neg1,
-                                       neg2, mb1, mb2);
-            if (mode == 1 || mode == 3) {
-                if (mb1 <= G || (mode == 3 && mb2 <= G2)) {
-                    exact_steps<NT, R, JU, HM, false>(c0, c0 + CH, bxy, bz, lut, sC, col, ax, ay,
-                                                      az, hf, shift, base, top_idx, row_bytes, K,
-                                                      S, a0, b0, a_first, n_recheck);
-                } else {
-                    const unsigned ge1 = (unsigned)(R * CH) - neg1;
-                    const unsigned ge2 = mode == 3 ? (unsigned)(R * CH) - neg2 : 0u;
-                    hist_add<HM>(col + rlo, neg1);
-                    hist_add<HM>(col + rlo + row_bytes, ge1 - ge2);
-                    if (mode == 3) hist_add<HM>(col + rhi, ge2);
-                    n_span += R * CH;
-                }
-            }
-            continue;
-        }
+    }
+}
+
+// A job's R A points (the owner lane's group) from the FP32 copy.
+template <int NT, int R, int JU, int HM>
+__device__ __forceinline__ int job_points(unsigned job, unsigned sIJ, const Segment& S,
+                                          f2_t (&ax)[R / 2], f2_t (&ay)[R / 2],
+                                          f2_t (&az)[R / 2]) {
+    constexpr int TA = PairKernel<NT, R, JU, HM, 0>::TA, SA = 32 * R;
+    const int a_first = (int)((job >> 5) & 7u) * SA + (int)(job & 31u) * R;
+    load_group<R>(S.a32 + lds_s64(sIJ) * TA + a_first, ax, ay, az);
+    return a_first;
+}
+
+// A job of the pair-by-pair kind.
+template <int NT, int R, int JU, int HM>
+__device__ __forceinline__ void exact_job(unsigned job, unsigned sIJ, unsigned bxy, unsigned bz,
+                                          unsigned lut, unsigned sC, unsigned col,
+                                          const PairParams& p, const Segment& S,
+                                          unsigned& n_recheck) {
+    f2_t ax[R / 2], ay[R / 2], az[R / 2];
+    const int a_first = job_points<NT, R, JU, HM>(job, sIJ, S, ax, ay, az);
+    const int c = (int)((job >> 8) & 255u);
+    exact_chunk<NT, R, JU, HM>(c * kChunk, (JU * c) & (kChunk - 1), a_first, sIJ, bxy, bz, lut,
+                               sC, col, ax, ay, az, p, S, n_recheck);
+}
+
+// A job of kind T (two or three slots).  Two slots: d = s - mid per pair,
+// mid the middle of the edge's guard band [lo, hi] and G its half-width (both
+// exact: the band is narrow); |d| > G puts s outside the band, and then
+// d < 0 means below it.  Three slots: the same against two edges.  Returns
+// false if some value had |d| <= G (rare): nothing was counted, and the
+// chunk has to go pair by pair.
+template <int NT, int R, int JU, int HM>
+__device__ __forceinline__ bool span_job(int T, unsigned job, unsigned sIJ, unsigned bxy,
+                                         unsigned bz, unsigned band, unsigned col,
+                                         const Segment& S) {
+    constexpr int HCOLS = PairKernel<NT, R, JU, HM, 0>::HCOLS;
+    constexpr int row_shift = ilog2(HCOLS * 4);
+    constexpr unsigned NP = (unsigned)(R * kChunk);
+    constexpr unsigned row_bytes = HCOLS * 4u;
+    f2_t ax[R / 2], ay[R / 2], az[R / 2];
+    job_points<NT, R, JU, HM>(job, sIJ, S, ax, ay, az);
+    const int c = (int)((job >> 8) & 255u);
+    const int c0 = c * kChunk, rot = (JU * c) & (kChunk - 1);
+    const unsigned slot = (job >> 16) & 0x3FFFu;
+    const unsigned rlo = slot << row_shift;
+    const unsigned ea = band + 8u * slot;
+    unsigned lo1, hi1;
+    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo1), "=r"(hi1) : "r"(ea));
+    const float lo_f = __uint_as_float(lo1), hi_f = __uint_as_float(hi1);
+    const float mid = 0.5f * (lo_f + hi_f);
+    const float G = fmaxf(mid - lo_f, hi_f - mid);
+    const f2_t nmid = pack2(-mid, -mid);
+    if (T == kJobTwo) {
         unsigned negq[R / 2];
         float mbq[R / 2];
 #pragma unroll
@@ -1137,8 +1213,9 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
             mbq[q] = __int_as_float(0x7f800000);
         }
 #pragma unroll 2
-        for (int j = c0; j < c0 + CH; j += JU)
-            two_slot_step<R, JU>(bxy, bz, ax, ay, az, j, nmid, negq, mbq);
+        for (int t = 0; t < kChunk; t += JU)
+            two_slot_step<R, JU>(bxy, bz, ax, ay, az, chunk_point<JU>(c0, t, rot), nmid, negq,
+                                 mbq);
         unsigned neg = 0;
         float mb = __int_as_float(0x7f800000);
 #pragma unroll
@@ -1146,19 +1223,192 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
             neg += negq[q];
             mb = fminf(mb, mbq[q]);
         }
-        if (mode == 1) {
-            if (mb <= G) {
-                // rare: a value near the edge; this thread bins the chunk pair by pair
-                exact_steps<NT, R, JU, HM, false>(c0, c0 + CH, bxy, bz, lut, sC, col, ax, ay, az,
-                                                  hf, shift, base, top_idx, row_bytes, K, S, a0,
-                                                  b0, a_first, n_recheck);
-            } else {
-                hist_add<HM>(col + rlo, neg);
-                hist_add<HM>(col + rhi, (unsigned)(R * CH) - neg);
-                n_span += R * CH;
+        if (mb <= G) return false;
+        hist_add<HM>(col + rlo, neg);
+        hist_add<HM>(col + rlo + row_bytes, NP - neg);
+        return true;
+    }
+    unsigned lo2, hi2;
+    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo2), "=r"(hi2) : "r"(ea + 8u));
+    const float lo2_f = __uint_as_float(lo2), hi2_f = __uint_as_float(hi2);
+    const float mid2 = 0.5f * (lo2_f + hi2_f);
+    const float G2 = fmaxf(mid2 - lo2_f, hi2_f - mid2);
+    unsigned neg1 = 0, neg2 = 0;
+    float mb1 = __int_as_float(0x7f800000), mb2 = __int_as_float(0x7f800000);
+#pragma unroll 2
+    for (int t = 0; t < kChunk; t += JU)
+        three_slot_step<R, JU>(bxy, bz, ax, ay, az, chunk_point<JU>(c0, t, rot), nmid,
+                               pack2(-mid2, -mid2), neg1, neg2, mb1, mb2);
+    if (mb1 <= G || mb2 <= G2) return false;
+    hist_add<HM>(col + rlo, neg1);
+    hist_add<HM>(col + rlo + row_bytes, neg2 - neg1);
+    hist_add<HM>(col + rlo + 2u * row_bytes, NP - neg2);
+    return true;
+}
+
+// Adds a warp's count (lanes with flag set, times w) to a 64-bit shared
+// counter at address a (statistics only).
+__device__ __forceinline__ void warp_stat(unsigned a, bool flag, unsigned w) {
+    const unsigned m = __ballot_sync(0xffffffffu, flag);
+    if ((threadIdx.x & 31) == 0 && m)
+        asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(a),
+                     "l"((unsigned long long)__popc(m) * w)
+                     : "memory");
+}
+
+// A warp's share of one item with span binning: units of its own sub-tile
+// first, then those left of the others (shared counters at address units, one
+// per sub-tile).  Each lane classifies its group against every chunk of a
+// unit; a chunk in one slot is counted at once, the others become jobs (the
+// warp's rings at shared address ring, 32 words per kind).  At the end the
+// warp runs what is left in its rings, then the diagonal units of an auto
+// count it took (pair by pair, with the i < j mask).  The tile pair (I, J)
+// stays in shared memory (sIJ) and the statistics go to the block's shared
+// counters (stat: rechecks, span pairs, skipped pairs), so that the rounds
+// run with few live registers.
+template <int NT, int R, int JU, int HM>
+__device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigned sIJ,
+                                          unsigned bxy, unsigned bz, unsigned lut, unsigned caps,
+                                          unsigned band, unsigned sC, unsigned hist,
+                                          const PairParams& p, const Segment& S, bool diag,
+                                          unsigned stat) {
+    using PK = PairKernel<NT, R, JU, HM, 0>;
+    constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
+    constexpr int NW = NT / 32, SA = 32 * R, UPS = 4, UB = TB / UPS, CPU = UB / kChunk;
+    constexpr int row_shift = ilog2(HCOLS * 4);
+    constexpr unsigned NP = (unsigned)(R * kChunk);
+    static_assert(NW <= 8 && TB / kChunk <= 256 && UB % kChunk == 0 && kChunk % JU == 0 &&
+                      NW * UPS <= 32,
+                  "job fields");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned col = hist + 4u * (unsigned)tid;
+    const bool stats = p.stats != nullptr;
+    unsigned fills = 0;      // jobs waiting per kind, 8 bits each
+    unsigned diag_units = 0;  // diagonal units taken (bit sub UPS + u)
+    int k = 0, cap_sub = -1, cn = -1;  // cn: next chunk of the current unit, -1: none
+    float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (;;) {
+#pragma unroll 1
+        while (k < NW && cn < 0) {
+            const int sub = (warp + k) % NW;
+            unsigned u = 0;
+            if (lane == 0) u = atom_add_shared(units + 4u * (unsigned)sub, 1u);
+            u = __shfl_sync(0xffffffffu, u, 0);
+            if (u >= (unsigned)UPS) {
+                ++k;
+                continue;
+            }
+            const int ub = (int)u * UB;
+            if (diag && ub + UB <= sub * SA) continue;  // every pair has i >= j
+            if (diag && ub < (sub + 1) * SA) {
+                diag_units |= 1u << (sub * UPS + (int)u);
+                continue;
+            }
+            if (sub != cap_sub) {
+                f2_t ax[R / 2], ay[R / 2], az[R / 2];
+                load_group<R>(S.a32 + lds_s64(sIJ) * TA + sub * SA + lane * R, ax, ay, az);
+                ga = group_cap<R>(ax, ay, az);
+                cap_sub = sub;
+            }
+            cn = ub / kChunk;
+        }
+        const bool done = k == NW;
+        // the chunk's job word with its kind + 1 in bits 30-31 (0: none)
+        unsigned kj = 0;
+        if (!done) {
+            const int c = cn;
+            cn = (c + 1) % CPU == 0 ? -1 : c + 1;
+            const uint4 gbu = lds_u4(caps + 16u * (unsigned)c);
+            const float4 gb = make_float4(__uint_as_float(gbu.x), __uint_as_float(gbu.y),
+                                          __uint_as_float(gbu.z), __uint_as_float(gbu.w));
+            unsigned rlo = 0;
+            const int mode = span_class(ga, gb, lut, p.tab.shift, p.tab.base, p.tab.n_lut - 1,
+                                        row_shift, rlo);
+            if (mode == 0) hist_add<HM>(col + rlo, NP);
+            else
+                kj = job_word(lane, (warp + k) % NW, c, rlo >> row_shift) |
+                     ((unsigned)(mode == 1 ? kJobTwo + 1 : mode == 3 ? kJobThree + 1
+                                                                     : kJobExact + 1) << 30);
+            if (stats) {
+                warp_stat(stat + 8u, mode == 0, NP);
+                warp_stat(stat + 16u, mode == 0, NP);
             }
         }
+        // Ring steps: the two-slot ring, the pair-by-pair ring for the
+        // two-slot jobs that found a value near their edge, the three-slot
+        // ring, the same for its jobs, then the pair-by-pair ring for the
+        // chunk's own job.  One code path per kind of round.
+        unsigned fb = 0;  // this lane's job that has to go pair by pair (bit 30: valid)
+#pragma unroll 1
+        for (int st = 0; st < 5; ++st) {
+            const int T = (0x298 >> (2 * st)) & 3;  // rings 0, 2, 1, 2, 2
+            const bool from_fb = (st & 1) != 0;
+            const unsigned word = from_fb ? fb : kj;
+            const bool push = from_fb ? fb != 0u : (kj >> 30) == (unsigned)(T + 1);
+            if (from_fb) fb = 0u;
+            const bool flush = done && (T != kJobExact || st == 4);
+            const unsigned m = __ballot_sync(0xffffffffu, push);
+            const int fill = (int)((fills >> (8 * T)) & 255u);
+            const int n = __popc(m);
+            if (n == 0 && !(flush && fill > 0)) continue;
+            const unsigned rt = ring + 128u * (unsigned)T;
+            const int pos = fill + __popc(m & ((1u << lane) - 1u));
+            const unsigned job = word & 0x3FFFFFFFu;
+            if (push && pos < 32) sts_u32(rt + 4u * (unsigned)pos, job);
+            const int total = fill + n;
+            if (total < 32 && !flush) {
+                fills += (unsigned)n << (8 * T);
+                continue;
+            }
+            __syncwarp();
+            const unsigned run = lds_u32(rt + 4u * (unsigned)lane);
+            __syncwarp();
+            if (push && pos >= 32) sts_u32(rt + 4u * (unsigned)(pos - 32), job);
+            fills = (fills & ~(255u << (8 * T))) | ((unsigned)max(total - 32, 0) << (8 * T));
+            unsigned n_recheck = 0;
+            bool settled = false;
+            if (lane < total) {
+                if (T == kJobExact) {
+                    exact_job<NT, R, JU, HM>(run, sIJ, bxy, bz, lut, sC, col, p, S, n_recheck);
+                } else {
+                    settled = span_job<NT, R, JU, HM>(T, run, sIJ, bxy, bz, band, col, S);
+                    if (!settled) fb = run | (1u << 30);
+                }
+            }
+            if (stats) {
+                warp_stat(stat + 8u, settled, NP);
+                if (__any_sync(0xffffffffu, n_recheck != 0)) {
+                    unsigned long long v = n_recheck;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0)
+                        asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(stat), "l"(v) : "memory");
+                }
+            }
+        }
+        if (done) break;
     }
+    // the diagonal units taken: pair by pair, i < j
+#pragma unroll 1
+    while (diag_units) {
+        const int b = __ffs(diag_units) - 1;
+        diag_units &= diag_units - 1;
+        const int sub = b / UPS, ub = (b % UPS) * UB, a_first = sub * SA + lane * R;
+        const long long I = lds_s64(sIJ), J = lds_s64(sIJ + 8u);
+        f2_t ax[R / 2], ay[R / 2], az[R / 2];
+        load_group<R>(S.a32 + I * TA + a_first, ax, ay, az);
+        unsigned long long nr = 0;
+        tile_pass<NT, R, JU, HM, 0, true>(bxy, bz, lut, sC, hist, ax, ay, az, p, S, I, J, a_first,
+                                          ub, ub + UB, nr);
+        if (stats) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) nr += __shfl_xor_sync(0xffffffffu, nr, o);
+            if (lane == 0 && nr)
+                asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(stat), "l"(nr) : "memory");
+        }
+    }
+    __syncwarp();
 }
 
 template <int NT, int R, int JU, int HM, int DEF>
@@ -1168,6 +1418,8 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
     constexpr int NW = NT / 32, SA = 32 * R, UPS = 4, UB = TB / UPS;
     static_assert(TA == NW * SA && TB % UPS == 0, "units tile the item");
     __shared__ unsigned s_units[NW];
+    // span job rings (one per kind and warp) for the shapes that bin spans
+    __shared__ unsigned s_ring[(!DEF && HM != kHistWarp) ? NW * kJobKinds * 32 : 1];
     extern __shared__ __align__(16) unsigned char smem[];
     const int K = p.tab.K;
     ulonglong2* sBxy = reinterpret_cast<ulonglong2*>(smem);
@@ -1177,7 +1429,11 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
     double* sC = reinterpret_cast<double*>(sLut + p.tab.n_lut);
     uint2* sBand = reinterpret_cast<uint2*>(sC + (K + 2));
     unsigned* hist = reinterpret_cast<unsigned*>(sBand + (K + 2));
-    __shared__ long long s_item, s_I, s_J;
+    // the item and its tile pair (I, J), in two buffers by the parity of the
+    // block's item count: thread 0 writes the next item's pair while other
+    // warps may still read the current one
+    __shared__ long long s_item, s_IJ[2][2];
+    __shared__ unsigned long long s_stat[3];  // span-path rechecks, span pairs, skipped pairs
 
     const int tid = threadIdx.x;
     const unsigned row_bytes = HCOLS * 4u;
@@ -1189,6 +1445,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
         sBand[q] = make_uint2(p.tab.band[q][0], p.tab.band[q][1]);
     }
     for (int q = tid; q < (K + 2) * HCOLS; q += NT) hist[q] = 0u;
+    if (tid < 3) s_stat[tid] = 0ull;
 
     // the current count lives in shared memory; thread 0 switches it when an
     // item of another count is claimed, after the block flushed its columns
@@ -1198,7 +1455,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
     // only some of them (tile pairs wholly beyond the top edge are skipped)
     const long long n_launch =
         p.n_items_dev ? min(p.n_items, (long long)*p.n_items_dev) : p.n_items;
-    unsigned long long n_recheck = 0, n_items = 0, n_span = 0, n_skip = 0;
+    unsigned long long n_recheck = 0, n_items = 0;
     int since_flush = 0, cur_seg = -2;
     for (;;) {
         if (tid == 0) {
@@ -1222,8 +1479,8 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
                 if (G->item_list) local = G->item_list[local];
                 long long I, J;
                 item_to_tiles(local, G->tiles_a, G->tiles_b, G->is_auto, &I, &J);
-                s_I = I;
-                s_J = J;
+                s_IJ[n_items & 1][0] = I;
+                s_IJ[n_items & 1][1] = J;
             }
         }
         __syncthreads();  // s_item visible; previous item's shared reads finished
@@ -1241,7 +1498,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
             __syncthreads();
         }
         const Segment& S = sSeg;
-        const long long I = s_I, J = s_J;
+        const long long I = s_IJ[n_items & 1][0], J = s_IJ[n_items & 1][1];
         const float4* gB = S.b32 + J * TB;
 #pragma unroll 4
         for (int q = 0; q < R; ++q) {
@@ -1255,7 +1512,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
         __syncthreads();  // B tile staged, unit counters reset
         const unsigned a_bxy = smem_addr(sBxy), a_bz = smem_addr(sBz), a_lut = smem_addr(sLut),
                        a_cap = smem_addr(sCap), a_band = smem_addr(sBand),
-                       a_hist = smem_addr(hist);
+                       a_hist = smem_addr(hist), a_c = smem_addr(sC);
         // The item is split into units of one warp's worth of A points (SA =
         // 32 R consecutive points, a sub-tile) by a quarter of the B tile.  A
         // warp takes the units of its own sub-tile first, then those left of
@@ -1263,11 +1520,19 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
         // whatever the mix of cheap and costly units.
         const int lane = tid & 31, warp = tid >> 5;
         const bool diag = S.is_auto && I == J;
+        bool spans = false;
+        if constexpr (!DEF && HM != kHistWarp) spans = p.span && S.b_caps;
+        if constexpr (!DEF && HM != kHistWarp) {
+            if (spans)
+                span_item<NT, R, JU, HM>(smem_addr(s_units),
+                                         smem_addr(s_ring + warp * (kJobKinds * 32)),
+                                         smem_addr(s_IJ[n_items & 1]), a_bxy, a_bz, a_lut, a_cap, a_band, a_c,
+                                         a_hist, p, S, diag, smem_addr(s_stat));
+        }
         int cur = -1;
         f2_t ax[R / 2], ay[R / 2], az[R / 2];
-        float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
-        for (int k = 0; k < NW; ++k) {
+        for (int k = 0; k < NW && !spans; ++k) {
             const int sub = (warp + k) % NW;
 #pragma unroll 1
             for (;;) {
@@ -1279,35 +1544,17 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
                 const int jb = (int)u * UB, je = jb + UB;
                 if (diag && je <= sub * SA) continue;  // every pair has i >= j
                 if (sub != cur) {
-                    // The thread's A points are R consecutive points of the
-                    // spatial order (a compact group: see span_mode), packed
-                    // two by two for the FP32x2 instructions.  Each value goes
-                    // through an explicit add of +0 (exact; it only turns -0
-                    // into +0, which leaves every squared chord unchanged): the
-                    // packed operands then get registers of their own instead
-                    // of being formed in place from the vector-load
-                    // destinations, a layout measured to cost about a quarter
-                    // of the screening loop's throughput.
-                    const float4* gA = S.a32 + I * TA + a_first;
-#pragma unroll
-                    for (int q = 0; q < R / 2; ++q) {
-                        const float4 a = gA[2 * q];
-                        const float4 b = gA[2 * q + 1];
-                        ax[q] = pack2(__fadd_rn(a.x, 0.f), __fadd_rn(b.x, 0.f));
-                        ay[q] = pack2(__fadd_rn(a.y, 0.f), __fadd_rn(b.y, 0.f));
-                        az[q] = pack2(__fadd_rn(a.z, 0.f), __fadd_rn(b.z, 0.f));
-                    }
-                    ga = group_cap<R>(ax, ay, az);
+                    load_group<R>(S.a32 + I * TA + a_first, ax, ay, az);
                     cur = sub;
                 }
                 if (diag && jb < (sub + 1) * SA)
-                    tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, a_cap, a_band, sC, a_hist, ax,
-                                                        ay, az, ga, p, S, I, J, a_first, jb, je,
-                                                        n_recheck, n_span, n_skip);
+                    tile_pass<NT, R, JU, HM, DEF, true>(a_bxy, a_bz, a_lut, a_c, a_hist, ax, ay,
+                                                        az, p, S, I, J, a_first, jb, je,
+                                                        n_recheck);
                 else
-                    tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, a_cap, a_band, sC, a_hist, ax,
-                                                         ay, az, ga, p, S, I, J, a_first, jb, je,
-                                                         n_recheck, n_span, n_skip);
+                    tile_pass<NT, R, JU, HM, DEF, false>(a_bxy, a_bz, a_lut, a_c, a_hist, ax, ay,
+                                                         az, p, S, I, J, a_first, jb, je,
+                                                         n_recheck);
             }
         }
         ++n_items;
@@ -1321,18 +1568,16 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
     // all threads left the loop after the same barrier
     if (cur_seg != -2) flush_hist<NT, HCOLS>(hist, K, sSeg.counts);
     if (p.stats) {
-        unsigned long long v = n_recheck, sp = n_span, sk = n_skip;
+        unsigned long long v = n_recheck;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            v += __shfl_xor_sync(0xffffffffu, v, o);
-            sp += __shfl_xor_sync(0xffffffffu, sp, o);
-            sk += __shfl_xor_sync(0xffffffffu, sk, o);
-        }
-        if ((tid & 31) == 0) {
-            if (v) atomicAdd(p.stats + WTHETA_STAT_RECHECK, v);
-            if (sp) atomicAdd(p.stats + WTHETA_STAT_SPAN, sp);
-            // pairs of skipped chunks were never computed
-            if (sk) atomicAdd(p.stats + WTHETA_STAT_PAIRS, 0ull - sk);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0 && v) atomicAdd(p.stats + WTHETA_STAT_RECHECK, v);
+        if (tid == 0) {
+            // the span path's counts (the loop's last barrier ordered them)
+            if (s_stat[0]) atomicAdd(p.stats + WTHETA_STAT_RECHECK, s_stat[0]);
+            if (s_stat[1]) atomicAdd(p.stats + WTHETA_STAT_SPAN, s_stat[1]);
+            // pairs of chunks settled in one slot were never computed
+            if (s_stat[2]) atomicAdd(p.stats + WTHETA_STAT_PAIRS, 0ull - s_stat[2]);
         }
         if (tid == 0 && n_items) {
             atomicAdd(p.stats + WTHETA_STAT_TILES, n_items);
@@ -1611,12 +1856,15 @@ int launch_cull_batch(const CullSeg* cs, int n_segs, long long total, double the
 }
 
 unsigned long long per_item_bound(const Variant* v) {
-    // a thread evaluates R x TB pairs per unit of its own sub-tile and may
-    // take the units of every other sub-tile of the item (NT/32 of them), so
-    // a histogram cell gains at most NT/32 x R TB per item (private
-    // per-thread column), 32 times that for a per-warp column
-    return (v->hm == kHistWarp ? 32ull : 1ull) * (unsigned long long)(v->nt / 32) *
-           (unsigned long long)v->r * (unsigned long long)v->nt * (unsigned long long)v->r;
+    // A thread bins R x TB pairs per unit of its own sub-tile and may take
+    // the units of every other sub-tile of the item (NT/32 of them): NT/32 x
+    // R TB pairs of its own groups.  With span jobs it also runs at most one
+    // job (R x 32 pairs) per round of its warp: as many pairs again, plus one
+    // last partial round per kind of job.  A per-warp column gains 32 times
+    // as much.
+    const unsigned long long own = (unsigned long long)(v->nt / 32) * (unsigned long long)v->r *
+                                   (unsigned long long)v->nt * (unsigned long long)v->r;
+    return (v->hm == kHistWarp ? 32ull : 1ull) * (2ull * own + 3ull * 32ull * (unsigned)v->r);
 }
 
 Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
