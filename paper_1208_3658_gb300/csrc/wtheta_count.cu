@@ -1122,10 +1122,11 @@ __device__ __forceinline__ unsigned atom_add_shared(unsigned a, unsigned v) {
 
 // A chunk's pairs with the lane's R A points (tile positions a_first ..)
 // binned pair by pair through the table, values inside a guard band settled
-// in FP64.  The tile pair (I, J) is read from shared memory (sIJ) only for
+// in FP64: the chunk's points t0, t0 + ts, ... (in its rotated order).  The tile pair (I, J) is read from shared memory (sIJ) only for
 // those.
 template <int NT, int R, int JU, int HM>
-__device__ __forceinline__ void exact_chunk(int c0, int rot, int a_first, unsigned sIJ,
+__device__ __forceinline__ void exact_chunk(int c0, int rot, int t0, int ts, int a_first,
+                                            unsigned sIJ,
                                             unsigned bxy, unsigned bz, unsigned lut, unsigned sC,
                                             unsigned col, const f2_t (&ax)[R / 2],
                                             const f2_t (&ay)[R / 2], const f2_t (&az)[R / 2],
@@ -1137,7 +1138,7 @@ __device__ __forceinline__ void exact_chunk(int c0, int rot, int a_first, unsign
     const float hf = __uint_as_float(p.tab.h_top);
     const int shift = p.tab.shift, base = p.tab.base, top_idx = p.tab.n_lut - 1;
 #pragma unroll 1
-    for (int t = 0; t < kChunk; ++t) {
+    for (int t = t0; t < kChunk; t += ts) {
         const int j = chunk_point<JU>(c0, t, rot);
         float s[NV];
         chords<NT, R, 1, false>(s, bxy, bz, ax, ay, az, j, 0);
@@ -1164,46 +1165,50 @@ __device__ __forceinline__ int job_points(unsigned job, unsigned sIJ, const Segm
     return a_first;
 }
 
-// A job of the pair-by-pair kind.
+// A job of the pair-by-pair kind (the chunk's points t0, t0 + ts, ...).
 template <int NT, int R, int JU, int HM>
-__device__ __forceinline__ void exact_job(unsigned job, unsigned sIJ, unsigned bxy, unsigned bz,
-                                          unsigned lut, unsigned sC, unsigned col,
-                                          const PairParams& p, const Segment& S,
+__device__ __forceinline__ void exact_job(unsigned job, int t0, int ts, unsigned sIJ,
+                                          unsigned bxy, unsigned bz, unsigned lut, unsigned sC,
+                                          unsigned col, const PairParams& p, const Segment& S,
                                           unsigned& n_recheck) {
     f2_t ax[R / 2], ay[R / 2], az[R / 2];
     const int a_first = job_points<NT, R, JU, HM>(job, sIJ, S, ax, ay, az);
     const int c = (int)((job >> 8) & 255u);
-    exact_chunk<NT, R, JU, HM>(c * kChunk, (JU * c) & (kChunk - 1), a_first, sIJ, bxy, bz, lut,
-                               sC, col, ax, ay, az, p, S, n_recheck);
+    exact_chunk<NT, R, JU, HM>(c * kChunk, (JU * c) & (kChunk - 1), t0, ts, a_first, sIJ, bxy,
+                               bz, lut, sC, col, ax, ay, az, p, S, n_recheck);
 }
 
-// A job of kind T (two or three slots).  Two slots: d = s - mid per pair,
-// mid the middle of the edge's guard band [lo, hi] and G its half-width (both
-// exact: the band is narrow); |d| > G puts s outside the band, and then
-// d < 0 means below it.  Three slots: the same against two edges.  Returns
-// false if some value had |d| <= G (rare): nothing was counted, and the
-// chunk has to go pair by pair.
+// The middle of the guard band of edge k (band table at shared address band)
+// and the band's half-width.
+__device__ __forceinline__ float edge_mid(unsigned band, unsigned k, float& G) {
+    unsigned lo, hi;
+    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo), "=r"(hi) : "r"(band + 8u * k));
+    const float lo_f = __uint_as_float(lo), hi_f = __uint_as_float(hi);
+    const float mid = 0.5f * (lo_f + hi_f);
+    G = fmaxf(mid - lo_f, hi_f - mid);
+    return mid;
+}
+
+// A job of kind T (two or three slots) over the chunk's steps t0, t0 + ts,
+// ... (JU points each).  Two slots: d = s - mid per pair, mid the middle of
+// the edge's guard band; three slots: the same against two edges.  neg1 and
+// neg2 count the values with d < 0 for the first and second edge (neg2 = 0
+// for two slots), mb1 and mb2 keep the smallest |d|.
 template <int NT, int R, int JU, int HM>
-__device__ __forceinline__ bool span_job(int T, unsigned job, unsigned sIJ, unsigned bxy,
-                                         unsigned bz, unsigned band, unsigned col,
-                                         const Segment& S) {
-    constexpr int HCOLS = PairKernel<NT, R, JU, HM, 0>::HCOLS;
-    constexpr int row_shift = ilog2(HCOLS * 4);
-    constexpr unsigned NP = (unsigned)(R * kChunk);
-    constexpr unsigned row_bytes = HCOLS * 4u;
+__device__ __forceinline__ void span_part(int T, unsigned job, int t0, int ts, unsigned sIJ,
+                                          unsigned bxy, unsigned bz, unsigned band,
+                                          const Segment& S, unsigned& neg1, unsigned& neg2,
+                                          float& mb1, float& mb2) {
     f2_t ax[R / 2], ay[R / 2], az[R / 2];
     job_points<NT, R, JU, HM>(job, sIJ, S, ax, ay, az);
     const int c = (int)((job >> 8) & 255u);
     const int c0 = c * kChunk, rot = (JU * c) & (kChunk - 1);
     const unsigned slot = (job >> 16) & 0x3FFFu;
-    const unsigned rlo = slot << row_shift;
-    const unsigned ea = band + 8u * slot;
-    unsigned lo1, hi1;
-    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo1), "=r"(hi1) : "r"(ea));
-    const float lo_f = __uint_as_float(lo1), hi_f = __uint_as_float(hi1);
-    const float mid = 0.5f * (lo_f + hi_f);
-    const float G = fmaxf(mid - lo_f, hi_f - mid);
+    float G;
+    const float mid = edge_mid(band, slot, G);
     const f2_t nmid = pack2(-mid, -mid);
+    neg1 = neg2 = 0;
+    mb1 = mb2 = __int_as_float(0x7f800000);
     if (T == kJobTwo) {
         unsigned negq[R / 2];
         float mbq[R / 2];
@@ -1212,34 +1217,48 @@ __device__ __forceinline__ bool span_job(int T, unsigned job, unsigned sIJ, unsi
             negq[q] = 0;
             mbq[q] = __int_as_float(0x7f800000);
         }
-#pragma unroll 2
-        for (int t = 0; t < kChunk; t += JU)
+#pragma unroll 1
+        for (int t = t0; t < kChunk; t += ts)
             two_slot_step<R, JU>(bxy, bz, ax, ay, az, chunk_point<JU>(c0, t, rot), nmid, negq,
                                  mbq);
-        unsigned neg = 0;
-        float mb = __int_as_float(0x7f800000);
 #pragma unroll
         for (int q = 0; q < R / 2; ++q) {
-            neg += negq[q];
-            mb = fminf(mb, mbq[q]);
+            neg1 += negq[q];
+            mb1 = fminf(mb1, mbq[q]);
         }
-        if (mb <= G) return false;
-        hist_add<HM>(col + rlo, neg);
-        hist_add<HM>(col + rlo + row_bytes, NP - neg);
-        return true;
+        return;
     }
-    unsigned lo2, hi2;
-    asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(lo2), "=r"(hi2) : "r"(ea + 8u));
-    const float lo2_f = __uint_as_float(lo2), hi2_f = __uint_as_float(hi2);
-    const float mid2 = 0.5f * (lo2_f + hi2_f);
-    const float G2 = fmaxf(mid2 - lo2_f, hi2_f - mid2);
-    unsigned neg1 = 0, neg2 = 0;
-    float mb1 = __int_as_float(0x7f800000), mb2 = __int_as_float(0x7f800000);
-#pragma unroll 2
-    for (int t = 0; t < kChunk; t += JU)
+    const float mid2 = edge_mid(band, slot + 1u, G);
+#pragma unroll 1
+    for (int t = t0; t < kChunk; t += ts)
         three_slot_step<R, JU>(bxy, bz, ax, ay, az, chunk_point<JU>(c0, t, rot), nmid,
                                pack2(-mid2, -mid2), neg1, neg2, mb1, mb2);
-    if (mb1 <= G || mb2 <= G2) return false;
+}
+
+// Settles a two- or three-slot job from its counts (summed over the lanes
+// that shared it): |d| > G for every value puts each value outside its
+// edge's guard band, and then d < 0 means below the edge.  Returns false if
+// some value had |d| <= G (rare): nothing is counted, and the chunk has to go
+// pair by pair.
+template <int NT, int R, int JU, int HM>
+__device__ __forceinline__ bool span_settle(int T, unsigned job, unsigned band, unsigned col,
+                                            unsigned neg1, unsigned neg2, float mb1, float mb2) {
+    constexpr int HCOLS = PairKernel<NT, R, JU, HM, 0>::HCOLS;
+    constexpr int row_shift = ilog2(HCOLS * 4);
+    constexpr unsigned NP = (unsigned)(R * kChunk);
+    constexpr unsigned row_bytes = HCOLS * 4u;
+    const unsigned slot = (job >> 16) & 0x3FFFu;
+    const unsigned rlo = slot << row_shift;
+    float G, G2 = 0.f;
+    edge_mid(band, slot, G);
+    if (mb1 <= G) return false;
+    if (T == kJobTwo) {
+        hist_add<HM>(col + rlo, neg1);
+        hist_add<HM>(col + rlo + row_bytes, NP - neg1);
+        return true;
+    }
+    edge_mid(band, slot + 1u, G2);
+    if (mb2 <= G2) return false;
     hist_add<HM>(col + rlo, neg1);
     hist_add<HM>(col + rlo + row_bytes, neg2 - neg1);
     hist_add<HM>(col + rlo + 2u * row_bytes, NP - neg2);
@@ -1361,18 +1380,41 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
                 fills += (unsigned)n << (8 * T);
                 continue;
             }
+            // A full round gives each lane a job.  The last, partial round of
+            // a ring shares each job among ts lanes (ts a power of two), lane
+            // q % ts taking the job's steps q % ts, q % ts + ts, ...
+            int ts = 1;
+            if (total < 32)
+                ts = 1 << (31 - __clz(32 / total));
+            if (T != kJobExact) ts = min(ts, kChunk / JU);
+            const int jl = lane / ts, t0 = lane % ts;
             __syncwarp();
-            const unsigned run = lds_u32(rt + 4u * (unsigned)lane);
+            const unsigned run = lds_u32(rt + 4u * (unsigned)min(jl, 31));
             __syncwarp();
             if (push && pos >= 32) sts_u32(rt + 4u * (unsigned)(pos - 32), job);
             fills = (fills & ~(255u << (8 * T))) | ((unsigned)max(total - 32, 0) << (8 * T));
+            const bool active = jl < total;
             unsigned n_recheck = 0;
             bool settled = false;
-            if (lane < total) {
-                if (T == kJobExact) {
-                    exact_job<NT, R, JU, HM>(run, sIJ, bxy, bz, lut, sC, col, p, S, n_recheck);
-                } else {
-                    settled = span_job<NT, R, JU, HM>(T, run, sIJ, bxy, bz, band, col, S);
+            if (T == kJobExact) {
+                if (active)
+                    exact_job<NT, R, JU, HM>(run, t0, ts, sIJ, bxy, bz, lut, sC, col, p, S,
+                                             n_recheck);
+            } else {
+                unsigned neg1 = 0, neg2 = 0;
+                float mb1 = __int_as_float(0x7f800000), mb2 = mb1;
+                if (active)
+                    span_part<NT, R, JU, HM>(T, run, t0 * JU, ts * JU, sIJ, bxy, bz, band, S,
+                                             neg1, neg2, mb1, mb2);
+#pragma unroll 1
+                for (int o = ts >> 1; o > 0; o >>= 1) {
+                    neg1 += __shfl_xor_sync(0xffffffffu, neg1, o);
+                    neg2 += __shfl_xor_sync(0xffffffffu, neg2, o);
+                    mb1 = fminf(mb1, __shfl_xor_sync(0xffffffffu, mb1, o));
+                    mb2 = fminf(mb2, __shfl_xor_sync(0xffffffffu, mb2, o));
+                }
+                if (active && t0 == 0) {
+                    settled = span_settle<NT, R, JU, HM>(T, run, band, col, neg1, neg2, mb1, mb2);
                     if (!settled) fb = run | (1u << 30);
                 }
             }
