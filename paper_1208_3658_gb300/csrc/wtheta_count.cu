@@ -1354,6 +1354,27 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
                 warp_stat(stat + 16u, mode == 0, NP);
             }
         }
+        // Most chunks fill no ring: their jobs are appended at once and the
+        // warp takes the next chunk (fills stay below 64, so 8 bits each).
+        if (!done) {
+            const unsigned kind = kj >> 30;
+            const unsigned m1 = __ballot_sync(0xffffffffu, kind == 1u);
+            const unsigned m2 = __ballot_sync(0xffffffffu, kind == 2u);
+            const unsigned m3 = __ballot_sync(0xffffffffu, kind == 3u);
+            const unsigned nf = fills + (unsigned)__popc(m1) + ((unsigned)__popc(m2) << 8) +
+                                ((unsigned)__popc(m3) << 16);
+            if ((nf & 0x202020u) == 0u) {
+                if (kind != 0u) {
+                    const int T = (int)kind - 1;
+                    const unsigned mk = T == 0 ? m1 : T == 1 ? m2 : m3;
+                    const int pos = (int)((fills >> (8 * T)) & 255u) +
+                                    __popc(mk & ((1u << lane) - 1u));
+                    sts_u32(ring + 128u * (unsigned)T + 4u * (unsigned)pos, kj & 0x3FFFFFFFu);
+                }
+                fills = nf;
+                continue;
+            }
+        }
         // Ring steps: the two-slot ring, the pair-by-pair ring for the
         // two-slot jobs that found a value near their edge, the three-slot
         // ring, the same for its jobs, then the pair-by-pair ring for the
