@@ -360,15 +360,26 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(unsigned* __restrict__ 
 // sentinels.
 __global__ void k_gather_points(const double* __restrict__ xyz, long long stride, long long n,
                                 long long n_pad, const unsigned* __restrict__ order,
-                                float4* __restrict__ p32, int tag) {
+                                float4* __restrict__ p32, double* __restrict__ s64, int tag) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
          i += (long long)gridDim.x * blockDim.x) {
+        double x, y, z;
         if (i < n) {
             const long long j = order[i];
-            p32[i] = point32(xyz[j], xyz[stride + j], xyz[2 * stride + j], j);
+            x = xyz[j];
+            y = xyz[stride + j];
+            z = xyz[2 * stride + j];
+            p32[i] = point32(x, y, z, j);
         } else {
-            p32[i] = sentinel32(tag, i - n);
+            const float4 q = sentinel32(tag, i - n);
+            p32[i] = q;
+            x = q.x;
+            y = q.y;
+            z = q.z;
         }
+        s64[i] = x;
+        s64[n_pad + i] = y;
+        s64[2 * n_pad + i] = z;
     }
 }
 
@@ -672,13 +683,15 @@ __global__ void k_cull_prefix(Segment* __restrict__ segs, const CullSeg* __restr
 }
 
 // FP64 recheck: the definition's squared chord and slot for the pair of
-// sorted positions (ia, jb), found in the caller's FP64 arrays through the
-// original indices kept in the FP32 copies; c64 is the shared address of
-// the FP64 edges.
+// sorted positions (ia, jb), read from the FP64 copies in the spatial order,
+// or from the caller's FP64 arrays through the original indices kept in the
+// FP32 copies (S.sorted64 says which); c64 is the shared address of
+// the FP64 edges.  hint >= 0: the slot just below the one edge whose guard
+// band held the FP32 value (checked, else the edges are searched in order).
 __device__ __forceinline__ unsigned recheck_slot(const Segment& S, long long ia, long long jb,
-                                                 unsigned c64, int K) {
-    const long long i = __float_as_int(S.a32[ia].w);
-    const long long j = __float_as_int(S.b32[jb].w);
+                                                 unsigned c64, int K, int hint = -1) {
+    const long long i = (S.sorted64 & 1) ? ia : __float_as_int(S.a32[ia].w);
+    const long long j = (S.sorted64 & 2) ? jb : __float_as_int(S.b32[jb].w);
     const double* a = S.a64;
     const double* b = S.b64;
     const long long as = S.a64_stride, bs = S.b64_stride;
@@ -686,6 +699,15 @@ __device__ __forceinline__ unsigned recheck_slot(const Segment& S, long long ia,
     const double dy = __dsub_rn(a[as + i], b[bs + j]);
     const double dz = __dsub_rn(a[2 * as + i], b[2 * bs + j]);
     const double s = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (hint >= 0 && hint <= K) {
+        // the FP32 value lay in the guard band of edge `hint` alone: the slot
+        // is hint or hint + 1, confirmed against the neighbouring edges
+        if (s < lds_f64(c64 + 8u * (unsigned)hint)) {
+            if (hint == 0 || lds_f64(c64 + 8u * (unsigned)(hint - 1)) <= s) return (unsigned)hint;
+        } else if (hint == K || s < lds_f64(c64 + 8u * (unsigned)(hint + 1))) {
+            return (unsigned)hint + 1u;
+        }
+    }
     unsigned k = 0;
     while (k <= (unsigned)K && lds_f64(c64 + 8u * k) <= s) ++k;
     return k;  // K+1 = overflow
@@ -776,6 +798,7 @@ __device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsign
                                                  unsigned sC,
                                                  Cnt& n_recheck) {
     unsigned mask = 0;
+    int hint_v = -1, hint = -1;  // the first such value and its edge's lower slot
 #pragma unroll
     for (int v = 0; v < NV; ++v) {
         const unsigned bits = __float_as_uint(s[v]);
@@ -783,12 +806,17 @@ __device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsign
         if (bits >= e.x && bits <= e.y) {
             mask |= 1u << v;
             hist_add<HM>(col + e.w, 0xFFFFFFFFu);  // -1
+            if (hint_v < 0) {
+                hint_v = v;
+                hint = e.w == e.z + row_bytes ? (int)(e.z >> (__ffs(row_bytes) - 1)) : -1;
+            }
         }
     }
     while (mask) {
         const int v = __ffs(mask) - 1;
         mask &= mask - 1;
-        const unsigned slot = recheck_slot(S, a0 + v % R, bj + v / R, sC, K);
+        const unsigned slot =
+            recheck_slot(S, a0 + v % R, bj + v / R, sC, K, v == hint_v ? hint : -1);
         ++n_recheck;
         hist_add<HM>(col + slot * row_bytes, 1u);
     }
@@ -1837,6 +1865,7 @@ size_t prepare_bytes(long long n, long long n_pad, int is_xyz) {
     b += ((size_t)n_pad / 32 * 16 + 255) / 256 * 256;  // chunk bounding spheres
     b += order_bytes(n, 0);                            // the sort
     if (!is_xyz) b += ((size_t)n * 24 + 255) / 256 * 256;  // FP64 SoA
+    b += (size_t)n_pad * 24 + 256;                     // the same, in the spatial order
     return b;
 }
 
@@ -1858,18 +1887,21 @@ int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int 
         count_launch();
         x64 = x;
     }
+    if (!is_xyz) sp += ((size_t)n * 24 + 255) / 256 * 256;
+    double* s64 = (double*)sp;  // FP64 SoA in the spatial order (stride n_pad)
     const unsigned* order = nullptr;
     int rc = spatial_order(x64, stride, n, is_xyz, nullptr, 0, sort_scratch, sm_count, st, &order,
                            nullptr);
     if (rc) return rc;
     k_gather_points<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(x64, stride, n, n_pad, order,
-                                                                  p32, tag);
+                                                                  p32, s64, tag);
     k_chunk_caps<<<launch_grid(n_pad, sm_count), 256, 0, st>>>(p32, n, n_pad, c32);
     count_launch(2);
     out->p32 = p32;
     out->c32 = c32;
-    out->x64 = x64;
-    out->stride = stride;
+    out->x64 = s64;
+    out->stride = n_pad;
+    out->sorted = 1;
     return check_cuda(cudaGetLastError());
 }
 
@@ -1938,6 +1970,7 @@ Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long lo
     g.a32 = A.p32; g.b32 = B.p32; g.a64 = A.x64; g.b64 = B.x64;
     g.b_caps = B.c32;
     g.a64_stride = A.stride; g.b64_stride = B.stride;
+    g.sorted64 = (A.sorted ? 1 : 0) | (B.sorted ? 2 : 0);
     g.tiles_a = ta; g.tiles_b = tb;
     g.item_begin = item_begin;
     g.n_items = is_auto ? ta * (ta + 1) / 2 : ta * tb;

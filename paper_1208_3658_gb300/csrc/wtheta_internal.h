@@ -46,7 +46,7 @@ enum HistMode { kHistLane = 1, kHistWarp = 2, kHistLaneAtomic = 3 };
 struct Segment {
     const float4* a32;       // FP32 points (x, y, z, original index bits), tile-padded
     const float4* b32;
-    const double* a64;       // FP64 SoA in the original order, stride a64_stride
+    const double* a64;       // FP64 SoA, stride a64_stride (order: sorted64)
     const double* b64;
     long long a64_stride, b64_stride;
     long long tiles_a, tiles_b;
@@ -58,7 +58,7 @@ struct Segment {
     const unsigned* item_list;   // if set: the count's kept items (tile pairs not skipped)
     const float4* b_caps;    // bounding spheres of B's chunks of 32 sorted points, or null
     int is_auto;
-    int pad_;
+    int sorted64;            // bit 0 (a64), bit 1 (b64): in the spatial order, else original
 };
 
 // Bounding cap of one tile of spatially ordered points: unit centre and an
@@ -76,7 +76,7 @@ struct CullSeg {
     long long ta, tb;
     unsigned* list;
     int is_auto;
-    int pad_;
+    int sorted64;            // bit 0 (a64), bit 1 (b64): in the spatial order, else original
 };
 
 struct PairParams {
@@ -111,8 +111,9 @@ struct DeviceInfo {
 struct Prepared {
     const float4* p32 = nullptr;
     const float4* c32 = nullptr;   // bounding sphere of each chunk of 32 sorted points
-    const double* x64 = nullptr;
+    const double* x64 = nullptr;   // FP64 SoA (stride), in the spatial order if sorted
     long long stride = 0;
+    int sorted = 0;
 };
 
 // Host-side launch plumbing (wtheta_count.cu), shared by the single-count,
