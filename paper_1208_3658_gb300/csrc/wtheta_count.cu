@@ -1131,6 +1131,8 @@ __device__ __forceinline__ void load_group(const float4* __restrict__ gA, f2_t (
 // ---------------------------------------------------------------------------
 constexpr int kJobTwo = 0, kJobThree = 1, kJobExact = 2, kJobKinds = 3, kChunk = 32;
 
+// Bits 0-4 lane, 5-7 sub-tile, 8-15 chunk, 16-29 slot; the ring loop keeps
+// the job's kind + 1 in bits 30-31 of the word it carries.
 __device__ __forceinline__ unsigned job_word(int lane, int sub, int chunk, unsigned slot) {
     return (unsigned)lane | ((unsigned)sub << 5) | ((unsigned)chunk << 8) | (slot << 16);
 }
@@ -1150,8 +1152,8 @@ __device__ __forceinline__ unsigned atom_add_shared(unsigned a, unsigned v) {
 
 // A chunk's pairs with the lane's R A points (tile positions a_first ..)
 // binned pair by pair through the table, values inside a guard band settled
-// in FP64: the chunk's points t0, t0 + ts, ... (in its rotated order).  The tile pair (I, J) is read from shared memory (sIJ) only for
-// those.
+// in FP64: the chunk's points t0, t0 + ts, ... (in its rotated order).  The
+// tile pair (I, J) is read from shared memory (sIJ) only for those values.
 template <int NT, int R, int JU, int HM>
 __device__ __forceinline__ void exact_chunk(int c0, int rot, int t0, int ts, int a_first,
                                             unsigned sIJ,
