@@ -930,9 +930,11 @@ __device__ __forceinline__ float4 group_cap(const f2_t (&ax)[R / 2], const f2_t 
 //      edge's guard band;
 //   3  slots k, k+1, k+2, split by edges k and k+1: two comparisons per pair;
 //   2  anything else: bin pair by pair.
-// rlo is a byte offset of a slot's row, slot << row_shift.
+// rlo is a byte offset of a slot's row, slot << row_shift; a span wholly
+// above h_top (the top edge's band) is the overflow row trash at once.
 __device__ __forceinline__ int span_class(float4 ga, float4 gb, unsigned lut, int shift, int base,
-                                          int top_idx, int row_shift, unsigned& rlo) {
+                                          int top_idx, int row_shift, unsigned& rlo,
+                                          unsigned h_top, unsigned trash) {
     const float dx = ga.x - gb.x, dy = ga.y - gb.y, dz = ga.z - gb.z;
     const float dc = sqrtf(dx * dx + dy * dy + dz * dz);
     const float rr = (ga.w + gb.w) * (1.f + 1e-6f) + 1e-6f;
@@ -941,6 +943,10 @@ __device__ __forceinline__ int span_class(float4 ga, float4 gb, unsigned lut, in
     const float shi = hi * hi * (1.f + 1e-5f);
     if (!(ga.w <= 2.f && gb.w >= 0.f && gb.w <= 2.f)) return 2;  // padding (or NaN)
     const unsigned bl = __float_as_uint(slo), bh = __float_as_uint(shi);
+    if (bl > h_top) {  // every pair beyond the top edge's band: overflow (row trash)
+        rlo = trash;
+        return 0;
+    }
     const uint4 el = lut_entry(bl, lut, shift, base, top_idx);
     const uint4 eh = lut_entry(bh, lut, shift, base, top_idx);
     if (!(bl < el.x || bl > el.y) || !(bh < eh.x || bh > eh.y)) return 2;
@@ -1315,7 +1321,7 @@ __device__ __forceinline__ void warp_stat(unsigned a, bool flag, unsigned w) {
 // stays in shared memory (sIJ) and the statistics go to the block's shared
 // counters (stat: rechecks, span pairs, skipped pairs), so that the rounds
 // run with few live registers.
-template <int NT, int R, int JU, int HM>
+template <int NT, int R, int JU, int HM, bool ST>
 __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigned sIJ,
                                           unsigned bxy, unsigned bz, unsigned lut, unsigned caps,
                                           unsigned band, unsigned sC, unsigned hist,
@@ -1331,7 +1337,7 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
                   "job fields");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned col = hist + 4u * (unsigned)tid;
-    const bool stats = p.stats != nullptr;
+    const bool stats = ST && p.stats != nullptr;
     unsigned fills = 0;      // jobs waiting per kind, 8 bits each
     unsigned diag_units = 0;  // diagonal units taken (bit sub UPS + u)
     int k = 0, cap_sub = -1, cn = -1;  // cn: next chunk of the current unit, -1: none
@@ -1372,13 +1378,16 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
             const float4 gb = make_float4(__uint_as_float(gbu.x), __uint_as_float(gbu.y),
                                           __uint_as_float(gbu.z), __uint_as_float(gbu.w));
             unsigned rlo = 0;
+            const unsigned trash = (unsigned)(p.tab.K + 1) << row_shift;
             const int mode = span_class(ga, gb, lut, p.tab.shift, p.tab.base, p.tab.n_lut - 1,
-                                        row_shift, rlo);
-            if (mode == 0) hist_add<HM>(col + rlo, NP);
-            else
+                                        row_shift, rlo, p.tab.h_top, trash);
+            if (mode == 0) {
+                if (rlo != trash) hist_add<HM>(col + rlo, NP);  // the trash row is never read
+            } else {
                 kj = job_word(lane, (warp + k) % NW, c, rlo >> row_shift) |
                      ((unsigned)(mode == 1 ? kJobTwo + 1 : mode == 3 ? kJobThree + 1
                                                                      : kJobExact + 1) << 30);
+            }
             if (stats) {
                 warp_stat(stat + 8u, mode == 0, NP);
                 warp_stat(stat + 16u, mode == 0, NP);
@@ -1504,7 +1513,9 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
     __syncwarp();
 }
 
-template <int NT, int R, int JU, int HM, int DEF>
+// ST: with the span path's statistics code (a launch with p.stats set); the
+// build without it is the one launched when no statistics are asked for.
+template <int NT, int R, int JU, int HM, int DEF, bool ST>
 __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __grid_constant__ PairParams p) {
     using PK = PairKernel<NT, R, JU, HM, DEF>;
     constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
@@ -1617,7 +1628,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
         if constexpr (!DEF && HM != kHistWarp) spans = p.span && S.b_caps;
         if constexpr (!DEF && HM != kHistWarp) {
             if (spans)
-                span_item<NT, R, JU, HM>(smem_addr(s_units),
+                span_item<NT, R, JU, HM, ST>(smem_addr(s_units),
                                          smem_addr(s_ring + warp * (kJobKinds * 32)),
                                          smem_addr(s_IJ[n_items & 1]), a_bxy, a_bz, a_lut, a_cap, a_band, a_c,
                                          a_hist, p, S, diag, smem_addr(s_stat));
@@ -1694,8 +1705,15 @@ __global__ void k_finalize_segments(const Segment* __restrict__ segs, int n_segs
 // ---------------------------------------------------------------------------
 template <int NT, int R, int JU, int HM, int DEF>
 static Variant make_variant() {
-    return Variant{NT, R, JU, HM, DEF, &k_pairs<NT, R, JU, HM, DEF>,
+    constexpr bool spans = !DEF && HM != kHistWarp;  // only the span path has ST code
+    return Variant{NT, R, JU, HM, DEF, &k_pairs<NT, R, JU, HM, DEF, true>,
+                   spans ? &k_pairs<NT, R, JU, HM, DEF, false> : &k_pairs<NT, R, JU, HM, DEF, true>,
                    &PairKernel<NT, R, JU, HM, DEF>::smem_bytes};
+}
+
+// The build of v's kernel for a launch with these parameters.
+static void (*pair_kernel(const Variant* v, const PairParams& prm))(PairParams) {
+    return prm.stats ? v->kernel : v->kernel_fast;
 }
 
 // Instantiated shapes (tile = threads x points_per_thread).  Per-warp
@@ -1786,13 +1804,20 @@ int grid_for(const Variant* v, size_t smem, long long n_items, int sm_count, int
     {
         std::lock_guard<std::mutex> g(mu);
         if (cudaFuncSetAttribute((const void*)v->kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess ||
+            cudaFuncSetAttribute((const void*)v->kernel_fast,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem) != cudaSuccess)
             return WTHETA_ECUDA;
     }
     int per_sm = 0;
+    int per_sm_fast = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)v->kernel, v->nt,
-                                                      smem) != cudaSuccess)
+                                                      smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_fast, (const void*)v->kernel_fast,
+                                                      v->nt, smem) != cudaSuccess)
         return WTHETA_ECUDA;
+    per_sm = std::min(per_sm, per_sm_fast);  // one grid size for both builds
     per_sm = std::max(per_sm, 1);
     if (want_per_sm > 0) per_sm = std::min(per_sm, want_per_sm);
     long long g = (long long)per_sm * sm_count;
@@ -2106,7 +2131,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
         PairParams prm = make_params(v, tab, &seg, nullptr, 0, 0, n_items, cursor, stats);
         prm.n_items_dev = n_list;
         prm.span = !(tune && tune->span_bins == 2);
-        v->kernel<<<grid, v->nt, smem, st>>>(prm);
+        pair_kernel(v, prm)<<<grid, v->nt, smem, st>>>(prm);
         count_launch();
         rc = check_cuda(cudaGetLastError());
         if (!rc) {
@@ -2252,7 +2277,7 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
 
 int launch_pairs(const Variant* v, const PairParams& prm, int grid, size_t smem,
                  cudaStream_t st) {
-    v->kernel<<<grid, v->nt, smem, st>>>(prm);
+    pair_kernel(v, prm)<<<grid, v->nt, smem, st>>>(prm);
     count_launch();
     return check_cuda(cudaGetLastError());
 }
@@ -2412,7 +2437,7 @@ static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double*
     B.p32 = b32; B.x64 = cb; B.stride = n_b;
     const Segment seg = make_segment(A, B, ta, tb, is_auto, 0, counts, total);
     const PairParams prm = make_params(v, tab, &seg, nullptr, 0, 0, n_items, cursor, nullptr);
-    v->kernel<<<grid, v->nt, smem, st>>>(prm);
+    pair_kernel(v, prm)<<<grid, v->nt, smem, st>>>(prm);
     count_launch();
     if ((rc = check_cuda(cudaGetLastError()))) return rc;
     k_finalize<<<1, 1, 0, st>>>(counts, K, total);
@@ -2607,7 +2632,7 @@ static int launch_batch_pairs(wtheta_plan* P, const Variant* v, long long item_b
                                  n_items, P->d_cursor, stats);
     prm.span = P->tune.span_bins != 2;
     prm.n_items_dev = n_items_dev;
-    v->kernel<<<grid, v->nt, smem, st>>>(prm);
+    pair_kernel(v, prm)<<<grid, v->nt, smem, st>>>(prm);
     count_launch();
     return check_cuda(cudaGetLastError());
 }

@@ -96,7 +96,8 @@ struct PairParams {
 
 struct Variant {
     int nt, r, ju, hm, def;
-    void (*kernel)(PairParams);
+    void (*kernel)(PairParams);       // the build with statistics code
+    void (*kernel_fast)(PairParams);  // the build launched without statistics
     size_t (*smem)(int, int);
 };
 
