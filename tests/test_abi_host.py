@@ -160,6 +160,34 @@ def test_guard_band_classification_is_sound(lo, hi, K, mode):
     assert n_in_band < total  # the band is narrow: most offsets >= 1e-5 resolve in FP32
 
 
+@pytest.mark.parametrize("lo,hi,K,mode", EDGE_SETS)
+def test_value_in_a_band_lies_between_the_neighbouring_edges(lo, hi, K, mode):
+    """The premise of the recheck's hint: an FP32 value inside edge k's guard
+    band has its FP64 squared chord in slot k or k+1, c[k-1] <= s64 < c[k+1]
+    (so the FP64 recheck compares with at most three edges)."""
+    rng = np.random.default_rng(777 + K)
+    e = W.wtheta_edges(lo, hi, K, mode)
+    c = W.wtheta_chord2_edges(e)
+    lo_b, hi_b, _ = W.wtheta_guard_band(e)
+    n_in = 0
+    for k in range(K + 1):
+        if e[k] == 0.0:
+            continue
+        rel = np.concatenate([-np.logspace(-12, -4, 400), np.logspace(-12, -4, 400)])
+        theta = np.clip(e[k] * (1 + rel), 1e-9, 180.0)
+        A, B = _pairs_at(theta, rng)
+        s32 = _emulate_s32(A, B)
+        s64 = _s64(A, B)
+        bits = s32.view(np.uint32)
+        inside = (bits >= lo_b[k]) & (bits <= hi_b[k])
+        below_edge = -np.inf if k == 0 else c[k - 1]
+        above_edge = np.inf if k == K else c[k + 1]
+        assert np.all(s64[inside] >= below_edge), k
+        assert np.all(s64[inside] < above_edge), k
+        n_in += int(inside.sum())
+    assert n_in > 0
+
+
 def test_fp32_error_bound_random_pairs():
     """|s32 - s64| <= g(c)/2 whenever c <= s64 <= 2c, over pairs at all
     scales (the half-width doubles the bound E(s), evaluated at 2c)."""
