@@ -330,3 +330,36 @@ def test_fused_edge_difference_classifies_exactly(lo, hi, K, mode):
         assert np.all((d[out] > 0) == (s64[out] >= c[k])), k
         decided += int(out.sum())
     assert decided > 0
+
+
+@pytest.mark.parametrize("lo,hi,K,mode", EDGE_SETS)
+def test_three_slot_difference_classifies_exactly(lo, hi, K, mode):
+    """The three-slot jobs compute s as the pair-by-pair path does and then
+    d = fl32(s - mid) for each of their two edges; outside |d| <= G the sign of
+    d must give the side of the FP64 squared chord, for pairs placed around
+    every edge, and for one edge evaluated beside its neighbour."""
+    rng = np.random.default_rng(4242 + K)
+    e = W.wtheta_edges(lo, hi, K, mode)
+    c = W.wtheta_chord2_edges(e)
+    lo_b, hi_b, _ = W.wtheta_guard_band(e)
+    decided = 0
+    for k in range(K + 1):
+        if e[k] == 0.0:
+            continue
+        rel = np.concatenate([-np.logspace(-12, -1, 500), np.logspace(-12, -1, 500)])
+        theta = np.clip(e[k] * (1 + rel), 1e-9, 180.0)
+        A, B = _pairs_at(theta, rng)
+        s32 = _emulate_s32(A, B)
+        s64 = _s64(A, B)
+        for q in (k, k + 1):  # this edge, and the next one seen from these pairs
+            if q > K or e[q] == 0.0:
+                continue
+            lo_f = np.array([lo_b[q]], np.uint32).view(np.float32)[0]
+            hi_f = np.array([hi_b[q]], np.uint32).view(np.float32)[0]
+            mid = np.float32(np.float32(0.5) * (lo_f + hi_f))
+            G = max(np.float32(mid - lo_f), np.float32(hi_f - mid))
+            d = (s32 - mid).astype(np.float32)
+            out = np.abs(d) > G
+            assert np.all((d[out] > 0) == (s64[out] >= c[q])), (k, q)
+            decided += int(out.sum())
+    assert decided > 0
