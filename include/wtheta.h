@@ -387,8 +387,11 @@ int wtheta_server_destroy(wtheta_server* server);
  * WTHETA_ESIZE and nothing is launched.
  *
  * The first call on a device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call on each device
- * before any stream capture.  Every call reuses the same array, which keeps
+ * device current (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call on each device before any stream capture.
+ * A device reset (cudaDeviceReset) or anything else that unloads the
+ * library's module from a device invalidates that address: do not call this
+ * entry point on a device after resetting it.  Every call reuses the same array, which keeps
  * the previous call's contents (each call rewrites what it reads and clears
  * its cursor): calls whose work can overlap on the GPU, from several streams
  * or host threads, race on the array and give wrong counts, so serialise them.
@@ -434,7 +437,8 @@ int wtheta_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_
  * Cross-correlation form of the same estimator between catalogues 1 and 2
  * with their randoms: w = (d1d2 - d1r2 - r1d2 + r1r2) / r1r2, each count
  * normalised by the product of its catalogue sizes, evaluated in that order.
- * Host arrays of K+2 slots; w: host, K doubles.
+ * Host arrays of K+2 slots; w: host, K doubles.  Bins with R1R2_k = 0 give
+ * NaN.
  */
 int wtheta_ls_cross(const uint64_t* D1D2, const uint64_t* D1R2, const uint64_t* R1D2,
                     const uint64_t* R1R2, int64_t n_d1, int64_t n_d2, int64_t n_r1,

@@ -146,16 +146,30 @@ def count(ra_dec_a: np.ndarray, ra_dec_b: np.ndarray | None, edges_deg: np.ndarr
 
 
 def ambiguity_tau(c: np.ndarray) -> np.ndarray:
-    """Width around each squared-chord edge inside which a few-ulp change of the
-    FP64 unit vectors (|dx_i| <= 8 ulp) can move a pair across the edge:
-    2 sqrt(3 s) 2^-49 + 12 u64 s, taken with margin as 2^-46 (sqrt(c) + c)."""
-    return 2.0 ** -46 * (np.sqrt(c) + c) + 2.0 ** -90
+    """Width around each squared-chord edge inside which moving every
+    component of both unit vectors by up to 8 ulps (the device's RA/Dec
+    conversion stays within 4 ulps of the host's) can move a pair across the
+    edge.  With every component of magnitude below 1 an ulp is at most 2^-53,
+    so the difference vector changes by |D| <= sqrt(3) 16 2^-53 = sqrt(3) 2^-49,
+    and s = |d|^2 by at most 2 |d| |D| + |D|^2 = 2 sqrt(3 s) 2^-49 + 3 2^-98,
+    plus the FP64 roundings of the two evaluations of s (each of d_i, its
+    square and the two sums rounds once: about 5 2^-53 s each, 10 2^-53 s
+    together).  Taken as 2^-47 (sqrt(c) + c/4) + 2^-90, which covers those
+    terms (2 sqrt(3) 2^-49 < 2^-47 and 10 2^-53 < 2^-47 / 4) with about 13% to
+    spare at the sqrt(c) term; the pin in
+    tests/oracle_pins.py perturbs pairs placed around every edge and checks
+    both that every slot change is flagged and that the width is no more than
+    about twice what the perturbations reach."""
+    return 2.0 ** -47 * (np.sqrt(c) + 0.25 * c) + 2.0 ** -90
 
 
-def count_ambiguous_xyz(xyz_a, xyz_b, edges_deg, is_auto, nthreads: int = 0) -> int:
+def count_ambiguous_xyz(xyz_a, xyz_b, edges_deg, is_auto, nthreads: int = 0,
+                        tau: np.ndarray | None = None) -> int:
+    """Pairs whose FP64 squared chord lies within tau_k (default
+    ambiguity_tau) of some edge c_k."""
     K = len(edges_deg) - 1
     c = chord2(edges_deg)
-    tau = ambiguity_tau(c)
+    tau = ambiguity_tau(c) if tau is None else np.ascontiguousarray(tau, np.float64)
     A = np.ascontiguousarray(xyz_a, np.float64)
     B = A if (is_auto or xyz_b is None) else np.ascontiguousarray(xyz_b, np.float64)
     out = np.zeros(1, np.uint64)

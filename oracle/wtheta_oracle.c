@@ -172,7 +172,8 @@ int orc_count_ambiguous(const double* xyz_a, int64_t na, const double* xyz_b, in
 
 /* Landy-Szalay, Eq. 2, each count normalised by its pair total:
  *   dd = DD/(n_d(n_d-1)/2), dr = DR/(n_d n_r), rr = RR/(n_r(n_r-1)/2),
- *   w = (dd - 2 dr + rr) / rr  for bins 1..K (slots 0 and K+1 are not bins). */
+ *   w = (dd - 2 dr + rr) / rr  for bins 1..K (slots 0 and K+1 are not bins);
+ * NaN where RR_k = 0 (the estimator divides by it). */
 int orc_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR,
            int64_t nd, int64_t nr, int K, double* w) {
     if (nd < 2 || nr < 2 || K < 1) return -1;
@@ -183,13 +184,15 @@ int orc_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR,
         double dd = (double)DD[k] / Ndd;
         double dr = (double)DR[k] / Ndr;
         double rr = (double)RR[k] / Nrr;
-        w[k - 1] = ((dd - 2.0 * dr) + rr) / rr;
+        /* no random pairs in the bin: Eq. 2 has no value there */
+        w[k - 1] = RR[k] ? ((dd - 2.0 * dr) + rr) / rr : NAN;
     }
     return 0;
 }
 
 /* Cross-correlation form of the same estimator between catalogues 1 and 2:
- *   w = (d1d2 - d1r2 - r1d2 + r1r2) / r1r2, each count over its n_a n_b. */
+ *   w = (d1d2 - d1r2 - r1d2 + r1r2) / r1r2, each count over its n_a n_b;
+ * NaN where R1R2_k = 0. */
 int orc_ls_cross(const uint64_t* D1D2, const uint64_t* D1R2, const uint64_t* R1D2,
                  const uint64_t* R1R2, int64_t nd1, int64_t nd2, int64_t nr1,
                  int64_t nr2, int K, double* w) {
@@ -199,7 +202,7 @@ int orc_ls_cross(const uint64_t* D1D2, const uint64_t* D1R2, const uint64_t* R1D
         double b = (double)D1R2[k] / ((double)nd1 * (double)nr2);
         double c = (double)R1D2[k] / ((double)nr1 * (double)nd2);
         double d = (double)R1R2[k] / ((double)nr1 * (double)nr2);
-        w[k - 1] = (((a - b) - c) + d) / d;
+        w[k - 1] = R1R2[k] ? (((a - b) - c) + d) / d : NAN;
     }
     return 0;
 }

@@ -2386,6 +2386,9 @@ static int count_xyz_noalloc_impl(const double* ca, long long n_a, const double*
         return WTHETA_EINVAL;
     }
     const long long T = WTHETA_NOALLOC_TILE;
+    // each size alone first, so that the rounding below cannot overflow
+    if (n_a > (long long)WTHETA_NOALLOC_MAX_POINTS || n_b > (long long)WTHETA_NOALLOC_MAX_POINTS)
+        return WTHETA_ESIZE;
     const long long pa = round_up(n_a, T), pb = is_auto ? 0 : round_up(n_b, T);
     if (pa + pb > (long long)WTHETA_NOALLOC_MAX_POINTS) return WTHETA_ESIZE;
     static thread_local BinTable tab;

@@ -293,7 +293,8 @@ int wtheta_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_
         const double dd = (double)DD[k] / Ndd;
         const double dr = (double)DR[k] / Ndr;
         const double rr = (double)RR[k] / Nrr;
-        w[k - 1] = ((dd - 2.0 * dr) + rr) / rr;
+        // Eq. 2 divides by the random pairs of the bin: none, no estimate
+        w[k - 1] = RR[k] ? ((dd - 2.0 * dr) + rr) / rr : std::numeric_limits<double>::quiet_NaN();
     }
     return WTHETA_OK;
 }
@@ -332,7 +333,7 @@ int wtheta_ls_cross(const uint64_t* D1D2, const uint64_t* D1R2, const uint64_t* 
         const double b = (double)D1R2[k] / ((double)nd1 * (double)nr2);
         const double c = (double)R1D2[k] / ((double)nr1 * (double)nd2);
         const double d = (double)R1R2[k] / ((double)nr1 * (double)nr2);
-        w[k - 1] = (((a - b) - c) + d) / d;
+        w[k - 1] = R1R2[k] ? (((a - b) - c) + d) / d : std::numeric_limits<double>::quiet_NaN();
     }
     return WTHETA_OK;
 }

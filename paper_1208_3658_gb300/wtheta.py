@@ -278,6 +278,15 @@ def wtheta_count_xyz_noalloc(xyz_a, xyz_b, edges_deg, is_auto: bool, counts, str
     """wtheta_count_xyz without any device allocation: the library's fixed
     scratch array is used instead (see include/wtheta.h for its limit)."""
     e, ep = _host_f64(edges_deg)
+    for name, t in (("xyz_a", xyz_a), ("xyz_b", None if is_auto else xyz_b)):
+        if t is None:
+            continue
+        if getattr(t, "dim", lambda: 0)() != 2 or t.shape[0] != 3:
+            raise ValueError("%s must have shape (3, n): SoA unit vectors" % name)
+        if str(t.dtype) != "torch.float64":
+            raise ValueError("%s must be float64" % name)
+    if counts is None or counts.numel() != len(e) + 1:
+        raise ValueError("counts must have len(edges) + 1 = K + 2 slots")
     na = _n_points(xyz_a, 3)
     nb = na if is_auto else _n_points(xyz_b, 3)
     _check(lib().wtheta_count_xyz_noalloc(_dev_ptr(xyz_a), na, _dev_ptr(xyz_b), nb, ep, len(e) - 1,

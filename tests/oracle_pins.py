@@ -19,7 +19,14 @@ Sources of truth, none of them the oracle itself:
   - bruteforce_angles: App. A's formula (with atan2) in long double on small
     random catalogues agrees with the oracle's slots;
   - edges_*: the three binning modes of Sec. 2.1;
-  - chord_values: chord lengths of 60, 90 and 180 degrees.
+  - chord_values: chord lengths of 60, 90 and 180 degrees;
+  - ls_empty_bins: Eq. 2 on hand-made counts, with its value worked out by
+    hand, and no value (NaN) where the bin holds no random pairs;
+  - ambiguity_tau: pairs placed around every edge of the workloads' edge
+    sets, their unit vectors moved by up to 8 ulps per component (aligned
+    with the pair's difference, and at random): every pair whose slot moves is
+    one the oracle flags as ambiguous, and the flagged width is no more than
+    about twice the largest move the perturbations reach.
 """
 from __future__ import annotations
 
@@ -265,9 +272,103 @@ def check_chord_values():
     assert abs(cs - tr * tr * (1 - tr * tr / 12)) <= 1e-15 * cs
 
 
+def check_ls_empty_bins():
+    """Eq. 2 on hand-made counts with n_d = n_r = 3 (pair totals 3, 9, 3):
+    DD = 3, DR = 0, RR = 3 gives (1 - 0 + 1)/1 = 2; DD = 0, DR = 9, RR = 3
+    gives (0 - 2 + 1)/1 = -1; a bin with RR = 0 has no estimate (NaN),
+    whatever DD and DR hold.  The cross form with all sizes 2 (totals 4):
+    (4 - 0 - 0 + 4)/4 = 2, (0 - 4 - 4 + 4)/4 = -1, and NaN where R1R2 = 0."""
+    u = lambda *v: np.array((0,) + v + (0,), np.uint64)  # noqa: E731
+    w = O.ls(u(3, 0, 0, 3, 0), u(0, 9, 0, 9, 5), u(3, 3, 0, 0, 0), 3, 3)
+    assert w[0] == 2.0 and w[1] == -1.0, w
+    assert np.all(np.isnan(w[2:])), w
+    w = O.ls_cross(u(4, 0, 0, 4), u(0, 4, 0, 0), u(0, 4, 0, 0), u(4, 4, 0, 0), 2, 2, 2, 2)
+    assert w[0] == 2.0 and w[1] == -1.0, w
+    assert np.all(np.isnan(w[2:])), w
+
+
+# Edge sets of the workloads (lo, hi, K, mode) whose pairs the P2 tests compare.
+TAU_EDGE_SETS = [
+    (1.0 * ARCMIN, 5.0, 16, O.LN), (0.5 * ARCMIN, 20.0, 32, O.LN),
+    (0.2 * ARCMIN, 30.0, 64, O.LN), (1.0 * ARCMIN, 10.0, 24, O.LN),
+    (0.0, 180.0, 12, O.LINEAR),
+]
+
+
+def _ulp_move(x, k):
+    """x moved by k ulps (k an integer array, same shape)."""
+    out = x.copy()
+    for step in range(int(np.max(np.abs(k))) if k.size else 0):
+        up, down = k > step, k < -step
+        out = np.where(up, np.nextafter(out, np.inf), out)
+        out = np.where(down, np.nextafter(out, -np.inf), out)
+    return out
+
+
+def _slot(a, b, e):
+    return int(np.argmax(O.count_xyz(a.reshape(3, 1), b.reshape(3, 1), e, False, nthreads=1)))
+
+
+def _flagged(a, b, e, tau):
+    return O.count_ambiguous_xyz(a.reshape(3, 1), b.reshape(3, 1), e, False, nthreads=1,
+                                 tau=tau) > 0
+
+
+def check_ambiguity_tau(scale: float = 1.0):
+    """The ambiguity width tau_k of the P2 comparisons (device unit vectors
+    within a few ulps of the host's).  For each edge c_k a pair (a, b) is
+    placed with s = c_k + f W_k, W_k = 2 sqrt(3 c_k) 2^-49 the largest first-
+    order move of s when every component of a and b moves by 8 ulps of 2^-53,
+    for f in +-{0.3 ... 1.2} and +-3; a has all components near 1/sqrt(3)
+    (ulps of 2^-53) and b lies along the tangent (1, 1, -2) direction, so that
+    moving each component by 8 ulps against (or with) the sign of a_i - b_i
+    reaches about 94% of W_k.  Checked: (1) every perturbed pair whose oracle
+    slot differs from the unperturbed pair's is flagged (|s - c_k| <= tau_k);
+    (2) some slot change happens at |s - c_k| > tau_k / 2, so that half the
+    width would miss it; (3) pairs at |s - c_k| >= 2.5 W_k are not flagged.
+    scale multiplies the width (a test plants scaled widths to see them fail)."""
+    rng = np.random.default_rng(11)
+    far_flip = False
+    n_flips = 0
+    for lo, hi, K, mode in TAU_EDGE_SETS:
+        e = O.edges(lo, hi, K, mode)
+        c = O.chord2(e)
+        tau = O.ambiguity_tau(c) * scale
+        for k in range(K + 1):
+            if not (0.0 < c[k] < 3.9):
+                continue
+            W = 2.0 * math.sqrt(3.0 * c[k]) * 2.0 ** -49
+            for f in (-3.0, -1.2, -0.9, -0.75, -0.6, -0.45, -0.3, 0.3, 0.45, 0.6, 0.75, 0.9, 1.2, 3.0):
+                a = np.array([1.0, 1.0, 1.0]) + rng.uniform(-0.02, 0.02, 3)
+                a /= np.linalg.norm(a)
+                t = np.array([1.0, 1.0, -2.0])
+                t -= a * np.dot(a, t)
+                t /= np.linalg.norm(t)
+                th = 2.0 * math.asin(math.sqrt(c[k] + f * W) / 2.0)
+                b = math.cos(th) * a + math.sin(th) * t
+                d = a - b
+                s0 = ((d[0] * d[0]) + (d[1] * d[1])) + (d[2] * d[2])
+                slot0 = _slot(a, b, e)
+                flag0 = _flagged(a, b, e, tau)
+                if abs(f) >= 3.0 and abs(s0 - c[k]) >= 2.5 * W:
+                    assert not flag0, ("flagged far from the edge", k, f, s0 - c[k], tau[k])
+                moves = [(8 * np.sign(d), -8 * np.sign(d)), (-8 * np.sign(d), 8 * np.sign(d))]
+                moves += [(rng.integers(-8, 9, 3), rng.integers(-8, 9, 3)) for _ in range(3)]
+                for ka, kb in moves:
+                    a1 = _ulp_move(a, ka.astype(np.int64))
+                    b1 = _ulp_move(b, kb.astype(np.int64))
+                    if _slot(a1, b1, e) != slot0:
+                        n_flips += 1
+                        assert flag0, ("slot moved but not flagged", k, f, s0 - c[k], tau[k])
+                        far_flip |= abs(s0 - c[k]) > 0.5 * tau[k]
+    assert n_flips > 100, n_flips
+    assert far_flip, "no slot change beyond half the width: the width is loose"
+
+
 ALL_CHECKS = [
     check_hand_placed, check_totals, check_dr_rd, check_d_equals_r,
     check_r_is_d_twice, check_estimators_closed_forms, check_regions_and_jackknife,
     check_cross_identity, check_analytic_rr,
     check_bruteforce_angles, check_edges_modes, check_chord_values,
+    check_ls_empty_bins, check_ambiguity_tau,
 ]

@@ -57,6 +57,37 @@ def test_ls_matches_oracle():
     assert np.allclose(wc[ok], wco[ok], rtol=1e-12, atol=0)
 
 
+def test_ls_empty_random_bins_give_nan():
+    """Eq. 2 divides by the bin's random pairs: where RR_k (or R1R2_k) is 0
+    the estimate is NaN, whatever DD and DR hold; elsewhere it is the value
+    worked out by hand (n_d = n_r = 3: totals 3, 9, 3)."""
+    u = lambda *v: np.array((0,) + v + (0,), np.uint64)  # noqa: E731
+    w = W.wtheta_ls(u(3, 0, 0, 3, 0), u(0, 9, 0, 9, 5), u(3, 3, 0, 0, 0), 3, 3)
+    assert w[0] == 2.0 and w[1] == -1.0
+    assert np.all(np.isnan(w[2:])), w
+    w = W.wtheta_ls_cross(u(4, 0, 0, 4), u(0, 4, 0, 0), u(0, 4, 0, 0), u(4, 4, 0, 0), 2, 2, 2, 2)
+    assert w[0] == 2.0 and w[1] == -1.0
+    assert np.all(np.isnan(w[2:])), w
+
+
+def test_noalloc_rejects_huge_sizes_before_any_device_work():
+    """Sizes past the fixed scratch's limit return WTHETA_ESIZE before any
+    rounding that could overflow, and before any CUDA call (so this runs
+    without a GPU): n near INT64_MAX would otherwise wrap when rounded up to
+    a whole tile."""
+    L = W.lib()
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    ep = e.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    c = ctypes.c_void_p(256)
+    ESIZE = -7
+    big = 2 ** 63 - 1
+    for na, nb, auto in [(big, big, 1), (big - 100, 0, 0), (5, big, 0), (big, 5, 0),
+                         (W.NOALLOC_MAX_POINTS + 1, 0, 1), (W.NOALLOC_MAX_POINTS, 1, 0)]:
+        b = None if auto else c
+        nb_ = na if auto else nb
+        assert L.wtheta_count_xyz_noalloc(c, na, b, nb_, ep, 16, auto, c, None) == ESIZE, (na, nb)
+
+
 def test_ls_closed_form_d_equals_r():
     """Counts with R = D give w = 2/n (derivation in oracle_pins)."""
     n = 500

@@ -29,13 +29,16 @@ MUTANTS = {
                        "double a = ra_dec[2 * i + 1] * (ORC_PI / 180.0);"),
     "last_column_dropped": ("for (int64_t j = j0; j < J->nb; ++j) {\n            double s = pair_s(J->A, J->na, i, J->B, J->nb, j);\n            J->hist[slot_of",
                             "for (int64_t j = j0; j + 1 < J->nb; ++j) {\n            double s = pair_s(J->A, J->na, i, J->B, J->nb, j);\n            J->hist[slot_of"),
-    "ls_dr_weight": ("w[k - 1] = ((dd - 2.0 * dr) + rr) / rr;", "w[k - 1] = ((dd - dr) + rr) / rr;"),
+    "ls_dr_weight": ("((dd - 2.0 * dr) + rr) / rr", "((dd - dr) + rr) / rr"),
     "ls_dd_total": ("double Ndd = (double)nd * (double)(nd - 1) / 2.0;",
                     "double Ndd = (double)nd * (double)(nd - 1);"),
     "ls_rr_uses_nd": ("double Nrr = (double)nr * (double)(nr - 1) / 2.0;",
                       "double Nrr = (double)nd * (double)(nd - 1) / 2.0;"),
-    "ls_divides_by_dd": ("w[k - 1] = ((dd - 2.0 * dr) + rr) / rr;", "w[k - 1] = ((dd - 2.0 * dr) + rr) / dd;"),
-    "ls_cross_sign": ("w[k - 1] = (((a - b) - c) + d) / d;", "w[k - 1] = (((a + b) - c) + d) / d;"),
+    "ls_divides_by_dd": ("((dd - 2.0 * dr) + rr) / rr", "((dd - 2.0 * dr) + rr) / dd"),
+    "ls_empty_bin_not_nan": ("RR[k] ? ((dd - 2.0 * dr) + rr) / rr : NAN", "((dd - 2.0 * dr) + rr) / rr"),
+    "ls_cross_sign": ("(((a - b) - c) + d) / d", "(((a + b) - c) + d) / d"),
+    "ls_cross_empty_bin_not_nan": ("R1R2[k] ? (((a - b) - c) + d) / d : NAN",
+                                   "(((a - b) - c) + d) / d"),
     "ls_cross_norm": ("double b = (double)D1R2[k] / ((double)nd1 * (double)nr2);",
                       "double b = (double)D1R2[k] / ((double)nd1 * (double)nd2);"),
     "log_edges_offset": ("e[k] = lo * exp((double)k * (log(hi / lo) / (double)K));",
@@ -74,4 +77,13 @@ def test_pins_catch_mutant(name):
                         check()
                 except (AssertionError, ValueError) as ex:  # noqa: PERF203
                     failed.append(check.__name__)
+                    break  # one failing pin is enough
         assert failed, f"no pin catches mutant {name}"
+
+
+@pytest.mark.parametrize("scale", [0.5, 2.5])
+def test_ambiguity_pin_catches_scaled_width(scale):
+    """The oracle's ambiguity width, halved or widened 2.5 times, fails its
+    pin (the mistake is planted in the oracle's width, on the CPU)."""
+    with pytest.raises(AssertionError):
+        oracle_pins.check_ambiguity_tau(scale)
