@@ -9,9 +9,13 @@ pair evaluations per second: (n(n-1)/2 + n n_r + n_r(n_r-1)/2) / step time.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload survey|small|largest]
 
-Under torchrun (N > 1) every rank counts its own independent w(theta) of the
-same shape (weak scaling, no collective on the data path); the step time is
-the maximum over ranks.  --impl reference times the CPU oracle instead, on a
+Under torchrun (N > 1) the survey w(theta) is sharded: every rank holds both
+whole catalogues, counts the pairs whose first point lies in its share of the
+tile rows (wtheta_count_wtheta_shard: rows split by kept tile pairs, so equal
+work), and one NCCL all-reduce of the 3 (K+2) counts combines them inside the
+timed step (strong scaling: the total work is fixed); the step time is the
+maximum over ranks.  --replicas runs N independent w(theta) instead (weak
+scaling, no collective).  --impl reference times the CPU oracle instead, on a
 bounded sample of the same workload, on the host cores.
 """
 from __future__ import annotations
@@ -62,6 +66,9 @@ def parse_args():
                          "prepared per call) instead of one wtheta_count_wtheta call")
     ap.add_argument("--no-span-bins", action="store_true",
                     help="bin every evaluated pair through the table (no per-chunk settling)")
+    ap.add_argument("--replicas", action="store_true",
+                    help="N > 1: independent replicas of the workload (weak scaling) instead "
+                         "of one w(theta) sharded over the ranks")
     ap.add_argument("--n", type=int, default=0,
                     help="points per catalogue (same shape, smaller: profiling cases)")
     return ap.parse_args()
@@ -234,7 +241,8 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
-    wl, desc = make_workload(args.workload, seed=1 + rank, n=args.n)
+    sharded = world > 1 and not args.replicas and not args.separate_counts
+    wl, desc = make_workload(args.workload, seed=1 if sharded else 1 + rank, n=args.n)
     e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
     K = wl.n_bins
     d_data = torch.from_numpy(wl.data).to(dev)
@@ -256,6 +264,17 @@ def run_ours(args, rank, world, dist):
     n_calls = 3 if args.separate_counts else 1
 
     def step(evs=None, stats=None):
+        if sharded:
+            # this rank's tile rows of every count, then one all-reduce of the
+            # 3 (K+2) counts over NCCL
+            if evs is not None:
+                evs[0][0].record(stream)
+            W.wtheta_count_wtheta_shard(d_data, d_rand, False, e, rank, world, counts, tune=tune,
+                                        stats=stats, stream=stream)
+            dist.all_reduce(counts, op=dist.ReduceOp.SUM)
+            if evs is not None:
+                evs[0][1].record(stream)
+            return
         if not args.separate_counts:
             # one w(theta): both catalogues prepared once, DD, DR, RR in one launch
             if evs is not None:
@@ -313,7 +332,7 @@ def run_ours(args, rank, world, dist):
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    value = world * pairs / (ms / 1e3)
+    value = (1 if sharded else world) * pairs / (ms / 1e3)
 
     # exactness checks on the benchmark's own output (cheap, exact integers)
     c = counts.cpu().numpy().astype(np.uint64)
@@ -366,7 +385,8 @@ def run_ours(args, rank, world, dist):
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "strong" if sharded else "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": desc, "n_data": nd, "n_rand": nr, "n_bins": K,
                    "tune": args.tune or "library default",
@@ -376,12 +396,14 @@ def run_ours(args, rank, world, dist):
                            "wtheta_count_wtheta (DD, DR, RR in one launch)"),
                    "pairs_per_step": pairs, "l2": "flushed between steps (512 MB write)",
                    "inputs": "resident in HBM (FP64 RA/Dec), converted inside each call",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": ("dp%d: tile rows sharded by kept tile pairs, NCCL all-reduce "
+                                   "of the counts" % world if sharded else
+                                   "replicas" if world > 1 else "single GPU")},
         "roofline": roofline,
         "gpu_launches": int(launches),
         "clocks": clocks,
         "counts_total_exact": bool(totals_ok),
-        "evaluated_pair_evals_per_s": world * evaluated / (ms / 1e3),
+        "evaluated_pair_evals_per_s": (1 if sharded else world) * evaluated / (ms / 1e3),
         "stats": {"in_range_frac": float(sum(int(x[:-1].sum()) for x in c)) / pairs,
                   "recheck_frac": float(st[W.STAT_RECHECK]) / max(1, float(pairs)),
                   "evaluated_over_algorithmic": float(st[W.STAT_PAIRS]) / pairs,
@@ -397,21 +419,40 @@ def run_ours(args, rank, world, dist):
         return out
     h_data = torch.from_numpy(wl.data).pin_memory()
     h_rand = torch.from_numpy(wl.rand).pin_memory()
-    W.wtheta_correlate(h_data.numpy(), h_rand.numpy(), e, stream=stream)
+
+    def e2e_step():
+        if not sharded:
+            W.wtheta_correlate(h_data.numpy(), h_rand.numpy(), e, stream=stream)
+            return
+        # each rank: pinned host catalogues in, its shard, the all-reduce, counts
+        # out, Eq. 2 on the host
+        dd = h_data.to(dev, non_blocking=True)
+        dr = h_rand.to(dev, non_blocking=True)
+        W.wtheta_count_wtheta_shard(dd, dr, False, e, rank, world, counts, stream=stream)
+        dist.all_reduce(counts, op=dist.ReduceOp.SUM)
+        hc = counts.cpu().numpy().astype(np.uint64)
+        W.wtheta_ls(hc[0], hc[1], hc[2], nd, nr)
+
+    e2e_step()
     e2e_t = []
     for _ in range(max(2, min(args.steps, 5))):
         torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
         t0 = time.perf_counter()
-        W.wtheta_correlate(h_data.numpy(), h_rand.numpy(), e, stream=stream)
+        e2e_step()
+        torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.mean(e2e_t)
     if dist is not None:
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    out["e2e"] = {"value": world * pairs / e2e_s, "unit": UNIT,
+    out["e2e"] = {"value": (1 if sharded else world) * pairs / e2e_s, "unit": UNIT,
                   "h2d_bytes_per_step": (nd + nr) * 16, "d2h_bytes_per_step": 3 * (K + 2) * 8,
-                  "api": "wtheta_correlate (pinned host RA/Dec in, counts + w out)",
+                  "api": ("per rank: pinned host RA/Dec in, wtheta_count_wtheta_shard, NCCL "
+                          "all-reduce, counts out, wtheta_ls" if sharded else
+                          "wtheta_correlate (pinned host RA/Dec in, counts + w out)"),
                   "skip_far_tile_pairs": True}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -156,6 +156,17 @@ int wtheta_count_shard(const double* ra_dec_a, int64_t n_a, const double* ra_dec
                        int32_t is_auto, int32_t shard, int32_t n_shards, uint64_t* counts,
                        void* stream);
 
+/*
+ * Contiguous split of n_rows weighted rows among n_shards: shard s gets rows
+ * [*row_begin, *row_end), the boundary before shard s being the first row
+ * whose prefix weight (the sum of the weights of the rows before it) reaches
+ * s/n_shards of the total; with all weights zero the rows are split evenly by
+ * number.  The ranges of shards 0..n_shards-1 partition [0, n_rows).  Host
+ * only.  weights: host, n_rows uint64.  EINVAL on bad arguments.
+ */
+int wtheta_shard_weights(const uint64_t* weights, int64_t n_rows, int32_t shard,
+                         int32_t n_shards, int64_t* row_begin, int64_t* row_end);
+
 /* Tuning knobs of the counting kernel; zero fields mean "choose". */
 typedef struct wtheta_tune {
     int32_t threads;           /* threads per block: 64, 128 or 256           */
@@ -213,6 +224,30 @@ int wtheta_count_wtheta(const double* coords_d, int64_t n_d, const double* coord
                         uint64_t* stats, void* stream);
 
 /*
+ * One shard of wtheta_count_wtheta, for one of n_shards GPUs or processes
+ * (the paper's summary notes that a straightforward division of the data set
+ * lets the code run on clusters of independent GPUs).  Every shard prepares
+ * both whole catalogues (replicas: no data moves between shards) and splits
+ * the tile rows of each count -- points of the count's first catalogue, in the
+ * library's spatial order, 1024 (or 512) to a row -- into n_shards contiguous
+ * ranges holding equal numbers of kept tile pairs (wtheta_shard_weights over
+ * the tile pairs whose bounding caps may meet below the top edge), so that
+ * shards of a clustered survey get equal work rather than equal pair totals.
+ * The shard counts the pairs whose first point lies in its rows; its 3 (K+2)
+ * counts (DD, DR, RR) are exact for those pairs, overflow slot included, and
+ * the counts of all shards add up, slot by slot (one sum-reduction of
+ * 3 (K+2) integers, e.g. an all-reduce), to those of wtheta_count_wtheta.
+ * The split is a deterministic function of the inputs, so every shard
+ * computes the same one.  Synchronises stream once (the kept tile pairs per
+ * row come to the host).  Other arguments as wtheta_count_wtheta; EINVAL
+ * unless 0 <= shard < n_shards.
+ */
+int wtheta_count_wtheta_shard(const double* coords_d, int64_t n_d, const double* coords_r,
+                              int64_t n_r, int32_t coords_are_xyz, const double* bin_edges_deg,
+                              int32_t n_bins, int32_t shard, int32_t n_shards, uint64_t* counts,
+                              const wtheta_tune* tune, uint64_t* stats, void* stream);
+
+/*
  * Batched counts: the DD, DR and RR of many (data, randoms) catalogue pairs
  * sharing one edge set, in one persistent launch captured in a CUDA graph.
  * The paper's §4 motivates it: Monte-Carlo error estimates of w(theta) need
@@ -244,6 +279,17 @@ typedef struct wtheta_plan wtheta_plan;
 int wtheta_batch_plan(const wtheta_catalog_pair* cats, int32_t n_cats,
                       const double* bin_edges_deg, int32_t n_bins, const wtheta_tune* tune,
                       void* stream, wtheta_plan** plan);
+
+/*
+ * As wtheta_batch_plan, with the catalogues given either as RA/Dec
+ * (coords_are_xyz = 0: interleaved FP64 degrees, converted on the device on
+ * every run) or as FP64 unit vectors (coords_are_xyz = 1: SoA, x[0..n),
+ * y[0..n), z[0..n) per catalogue), in which case the counts are a pure
+ * function of those bits, like wtheta_count_xyz's.
+ */
+int wtheta_batch_plan_ex(const wtheta_catalog_pair* cats, int32_t n_cats, int32_t coords_are_xyz,
+                         const double* bin_edges_deg, int32_t n_bins, const wtheta_tune* tune,
+                         void* stream, wtheta_plan** plan);
 
 /*
  * Runs a plan: one graph replay (conversion and spatial ordering of every

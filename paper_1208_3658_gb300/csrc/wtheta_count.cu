@@ -322,6 +322,94 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
     }
 }
 
+// The whole spatial order of a small catalogue (n <= kSmallSort) in one
+// block: the keys of k_sort_keys, then the same stable LSD radix sort (four
+// 8-bit passes; in each pass rounds of 1024 keys, ranked inside a warp by
+// __match_any_sync and across warps by per-warp digit counts) with keys and
+// 16-bit indices in shared memory.  One launch instead of thirteen.
+constexpr int kSmallSort = 12288;
+constexpr int kSmallSortThreads = 1024;
+constexpr size_t kSmallSortSmem =
+    (size_t)kSmallSort * (2 * 4 + 2 * 2) + (size_t)(kSmallSortThreads / 32) * 256 * 2 + 256 * 4;
+
+__global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(const double* __restrict__ xyz,
+                                                                  long long stride, int n,
+                                                                  int check,
+                                                                  unsigned* __restrict__ order) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    unsigned* key0 = reinterpret_cast<unsigned*>(sm);
+    unsigned* key1 = key0 + kSmallSort;
+    unsigned short* idx0 = reinterpret_cast<unsigned short*>(key1 + kSmallSort);
+    unsigned short* idx1 = idx0 + kSmallSort;
+    unsigned short* wcnt = idx1 + kSmallSort;                       // [warp][digit]
+    unsigned* base = reinterpret_cast<unsigned*>(wcnt + (kSmallSortThreads / 32) * 256);
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    constexpr int NW = kSmallSortThreads / 32;
+    for (int i = t; i < n; i += kSmallSortThreads) {
+        const double x = xyz[i], y = xyz[stride + i], z = xyz[2 * stride + i];
+        if (check) check_unit(x, y, z);
+        key0[i] = cell_key(x, y, z, kSortLevel);
+        idx0[i] = (unsigned short)i;
+    }
+    unsigned *kin = key0, *kout = key1;
+    unsigned short *iin = idx0, *iout = idx1;
+    for (int pass = 0; pass < 4; ++pass) {
+        const int shift = 8 * pass;
+        if (t < 256) base[t] = 0;
+        __syncthreads();
+        // digit totals, then their exclusive prefix (thread d owns digit d)
+        for (int i = t; i < n; i += kSmallSortThreads) atomicAdd(&base[(kin[i] >> shift) & 255u], 1u);
+        __syncthreads();
+        if (w == 0) {
+            unsigned run = 0;
+            for (int d0 = 0; d0 < 256; d0 += 32) {
+                const unsigned c = base[d0 + lane];
+                unsigned incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                base[d0 + lane] = run + incl - c;
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
+        __syncthreads();
+        for (int r0 = 0; r0 < n; r0 += kSmallSortThreads) {
+            for (int q = t; q < NW * 256; q += kSmallSortThreads) wcnt[q] = 0;
+            __syncthreads();
+            const int i = r0 + t;
+            const bool valid = i < n;
+            const unsigned k = valid ? kin[i] : 0u;
+            const unsigned d = valid ? (k >> shift) & 255u : 256u;
+            const unsigned peers = __match_any_sync(0xffffffffu, d);
+            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
+            if (valid && rank == 0) wcnt[w * 256 + d] = (unsigned short)__popc(peers);
+            __syncthreads();
+            if (t < 256) {
+                // warp q's keys of digit t go from wcnt[q][t] on (positions < 2^16)
+                unsigned acc = base[t];
+                for (int q = 0; q < NW; ++q) {
+                    const unsigned c = wcnt[q * 256 + t];
+                    wcnt[q * 256 + t] = (unsigned short)acc;
+                    acc += c;
+                }
+                base[t] = acc;
+            }
+            __syncthreads();
+            if (valid) {
+                const unsigned pos = (unsigned)wcnt[w * 256 + d] + rank;
+                kout[pos] = k;
+                iout[pos] = iin[i];
+            }
+            __syncthreads();
+        }
+        unsigned* tk = kin; kin = kout; kout = tk;
+        unsigned short* ti = iin; iin = iout; iout = ti;
+    }
+    for (int i = t; i < n; i += kSmallSortThreads) order[i] = iin[i];
+}
+
 // Exclusive prefix sum in place (one block of 1024).
 __global__ void __launch_bounds__(1024) k_exclusive_scan(unsigned* __restrict__ a, int n) {
     __shared__ unsigned warp_sum[32];
@@ -646,7 +734,7 @@ __global__ void k_cull_batch(const CullSeg* __restrict__ cs, int n_segs, long lo
                 if (cs[mid].begin <= g) lo = mid; else hi = mid - 1;
             }
             seg = lo;
-            local = g - cs[seg].begin;
+            local = g - cs[seg].begin + cs[seg].offset;
             long long I, J;
             item_to_tiles(local, cs[seg].ta, cs[seg].tb, cs[seg].is_auto, &I, &J);
             keep = caps_may_meet(cs[seg].ca[I], cs[seg].cb[J], theta_top);
@@ -663,6 +751,25 @@ __global__ void k_cull_batch(const CullSeg* __restrict__ cs, int n_segs, long lo
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) skipped += __shfl_xor_sync(0xffffffffu, skipped, o);
         if (lane == 0 && skipped) atomicAdd(stats + WTHETA_STAT_SKIPPED, skipped);
+    }
+}
+
+// Kept tile pairs per tile row of every count (rows[cs_row0[seg] + I]), for
+// splitting the rows of each count among shards by their work.
+__global__ void k_cull_rows(const CullSeg* __restrict__ cs, int n_segs, long long total,
+                            double theta_top, const long long* __restrict__ row0,
+                            unsigned long long* __restrict__ rows) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total; g += stride) {
+        int lo = 0, hi = n_segs - 1;  // last count with begin <= g
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cs[mid].begin <= g) lo = mid; else hi = mid - 1;
+        }
+        const long long local = g - cs[lo].begin + cs[lo].offset;
+        long long I, J;
+        item_to_tiles(local, cs[lo].ta, cs[lo].tb, cs[lo].is_auto, &I, &J);
+        if (caps_may_meet(cs[lo].ca[I], cs[lo].cb[J], theta_top)) atomicAdd(rows + row0[lo] + I, 1ull);
     }
 }
 
@@ -1861,6 +1968,17 @@ int spatial_order(const double* x64, long long stride, long long n, int check,
     *order = idx[0];
     if (sorted_labels) *sorted_labels = nullptr;
     if (n <= 0) return WTHETA_OK;
+    if (!labels && n <= kSmallSort) {
+        // small catalogue: the whole sort in one block
+        static const bool attr_ok =
+            cudaFuncSetAttribute((const void*)k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmallSortSmem) == cudaSuccess;
+        if (!attr_ok) return WTHETA_ECUDA;
+        k_sort_small<<<1, kSmallSortThreads, kSmallSortSmem, st>>>(x64, stride, (int)n, check,
+                                                                   idx[0]);
+        count_launch();
+        return check_cuda(cudaGetLastError());
+    }
     k_sort_keys<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, check, key[0], idx[0]);
     count_launch();
     for (int pass = 0; pass < 4; ++pass) {
@@ -2149,17 +2267,39 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     return rc;
 }
 
+// Pairs (i < j) of an auto count of n points whose first point i is in the
+// sorted rows [r0, r1).
+static unsigned long long auto_pairs_in_rows(long long n, long long r0, long long r1) {
+    if (r1 <= r0) return 0ull;
+    const unsigned long long a = (unsigned long long)r0, b = (unsigned long long)r1;
+    return (b - a) * (unsigned long long)(n - 1) - (b * (b - 1) / 2 - (a ? a * (a - 1) / 2 : 0ull));
+}
+
+// First item (tile pair) of tile row I: auto counts enumerate the upper
+// triangle row by row (row I holds t - I items), cross counts the rectangle.
+static long long row_item(long long I, long long ta, long long tb, int is_auto) {
+    return is_auto ? I * ta - I * (I - 1) / 2 : I * tb;
+}
+
 // The three counts of one w(theta) (DD, DR, RR) in one persistent launch:
 // each catalogue is prepared once, far tile pairs of each count are skipped
 // on the device, and the counts are three segments of one work table, so
 // there is one launch tail instead of three.  counts: device, 3 x (K+2).
+//
+// With n_shards > 1 only shard `shard` of each count is counted: the tile
+// rows of the count (points of its first catalogue in the spatial order) are
+// split into n_shards contiguous ranges holding equal numbers of kept tile
+// pairs (one synchronisation brings the kept tile pairs per row to the host),
+// and the shard counts the pairs whose first point lies in its rows, overflow
+// slot included; the shards' counts add up to the whole count.
 static int count_wtheta_impl(const double* cd, long long nd, const double* cr, long long nr,
                              int is_xyz, const double* edges, int K,
                              unsigned long long* counts, const wtheta_tune* tune,
-                             unsigned long long* stats, cudaStream_t st) {
+                             unsigned long long* stats, cudaStream_t st, int shard = 0,
+                             int n_shards = 1) {
     TraceRange trace("wtheta_count_wtheta");
     if (!counts || nd < 0 || nr < 0 || (nd > 0 && !cd) || (nr > 0 && !cr) ||
-        (is_xyz != 0 && is_xyz != 1))
+        (is_xyz != 0 && is_xyz != 1) || n_shards < 1 || shard < 0 || shard >= n_shards)
         return WTHETA_EINVAL;
     if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
                  tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
@@ -2183,8 +2323,13 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     const unsigned long long ndr = (unsigned long long)nd * (unsigned long long)nr;
     const unsigned long long nrr = (unsigned long long)nr * (unsigned long long)(nr > 0 ? nr - 1 : 0) / 2;
     // the counts with work, biggest first
-    struct Cnt { int kind; long long items; unsigned long long total; };
-    Cnt all[3] = {{0, td * (td + 1) / 2, ndd}, {1, td * tr, ndr}, {2, tr * (tr + 1) / 2, nrr}};
+    struct Cnt {
+        int kind;
+        long long items;            // tile pairs of the count (of the shard's rows)
+        unsigned long long total;   // pairs of the count (of the shard's rows)
+        long long offset;           // first item of the shard's rows
+    };
+    Cnt all[3] = {{0, td * (td + 1) / 2, ndd, 0}, {1, td * tr, ndr, 0}, {2, tr * (tr + 1) / 2, nrr, 0}};
     std::vector<Cnt> cnts;
     for (const Cnt& c : all)
         if (c.total > 0) cnts.push_back(c);
@@ -2196,7 +2341,7 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     const bool cull = (!tune || tune->skip_far != 2) && edges[K] < 180.0 && td * td < (1LL << 32) &&
                       td * tr < (1LL << 32) && tr * tr < (1LL << 32);
     // scratch: cursor and kept total, segments, culling table, kept counts,
-    // both prepared catalogues, tile caps, kept lists
+    // both prepared catalogues, tile caps, kept lists (and kept items per row)
     const size_t ba = prepare_bytes(nd, pd, is_xyz), bb = prepare_bytes(nr, pr, is_xyz);
     size_t bytes = 256 + 1024 + 1024 + 256;
     const size_t off_d = bytes;
@@ -2205,6 +2350,8 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     bytes += (bb + 255) / 256 * 256;
     const size_t off_caps = bytes;
     if (cull) bytes += ((size_t)(td + tr) * sizeof(TileCap) + 255) / 256 * 256;
+    const size_t off_rows = bytes;
+    if (n_shards > 1) bytes += ((size_t)(2 * td + tr) * 8 + 255) / 256 * 256 + 256;
     const size_t off_lists = bytes;
     if (cull) bytes += (size_t)total_items * 4;
     unsigned char* m = nullptr;
@@ -2220,9 +2367,69 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     if (!rc) rc = prepare(cr, nr, pr, is_xyz, 1, m + off_r, di.sm_count, st, &R);
     TileCap* caps_d = (TileCap*)(m + off_caps);
     TileCap* caps_r = caps_d + td;
-    if (!rc && cull) {
+    if (!rc && (cull || n_shards > 1)) {
         rc = launch_tile_caps(D.p32, nd, (int)T, td, caps_d, st);
         if (!rc) rc = launch_tile_caps(R.p32, nr, (int)T, tr, caps_r, st);
+    }
+    const double theta_top = edges[K] * (3.14159265358979323846 / 180.0);
+    auto cull_seg = [&](int i, long long begin) {
+        const int k = cnts[i].kind;
+        CullSeg c;
+        std::memset(&c, 0, sizeof(CullSeg));
+        c.begin = begin;
+        c.n = cnts[i].items;
+        c.offset = cnts[i].offset;
+        c.ta = k == 2 ? tr : td;
+        c.tb = k == 0 ? td : tr;
+        c.is_auto = k != 1;
+        c.ca = k == 2 ? caps_r : caps_d;
+        c.cb = k == 0 ? caps_d : caps_r;
+        return c;
+    };
+    if (!rc && n_shards > 1 && n_segs > 0) {
+        // kept tile pairs per tile row of every count (all tile pairs count when
+        // nothing is skipped), then this shard's rows of each count
+        long long row0[3], nrow[3], item = 0;
+        CullSeg cs[3];
+        for (int i = 0; i < n_segs; ++i) {
+            cs[i] = cull_seg(i, item);
+            item += cnts[i].items;
+            row0[i] = i == 0 ? 0 : row0[i - 1] + nrow[i - 1];
+            nrow[i] = cnts[i].kind == 2 ? tr : td;
+        }
+        unsigned long long* d_rows = (unsigned long long*)(m + off_rows);
+        long long* d_row0 = (long long*)(m + off_rows + ((size_t)(2 * td + tr) * 8 + 255) / 256 * 256);
+        const long long n_rows = row0[n_segs - 1] + nrow[n_segs - 1];
+        std::vector<unsigned long long> rows(n_rows);
+        rc = check_cuda(cudaMemsetAsync(d_rows, 0, (size_t)n_rows * 8, st));
+        if (!rc) rc = check_cuda(cudaMemcpyAsync(d_cull, cs, sizeof(CullSeg) * n_segs,
+                                                 cudaMemcpyHostToDevice, st));
+        if (!rc) rc = check_cuda(cudaMemcpyAsync(d_row0, row0, sizeof(row0), cudaMemcpyHostToDevice, st));
+        if (!rc) {
+            k_cull_rows<<<launch_grid(total_items, di.sm_count), 256, 0, st>>>(
+                d_cull, n_segs, total_items, cull ? theta_top : 4.0, d_row0, d_rows);
+            count_launch();
+            rc = check_cuda(cudaGetLastError());
+        }
+        if (!rc) rc = check_cuda(cudaMemcpyAsync(rows.data(), d_rows, (size_t)n_rows * 8,
+                                                 cudaMemcpyDeviceToHost, st));
+        if (!rc) rc = check_cuda(cudaStreamSynchronize(st));
+        for (int i = 0; i < n_segs && !rc; ++i) {
+            const int k = cnts[i].kind;
+            const int aut = k != 1;
+            long long I0 = 0, I1 = 0;
+            rc = wtheta_shard_weights((const uint64_t*)rows.data() + row0[i], nrow[i], shard, n_shards,
+                                      (int64_t*)&I0, (int64_t*)&I1);
+            const long long ta = k == 2 ? tr : td, tb = k == 0 ? td : tr;
+            const long long n_a = k == 2 ? nr : nd, n_b = k == 0 ? nd : nr;
+            const long long r0 = std::min(I0 * T, n_a), r1 = std::min(I1 * T, n_a);
+            cnts[i].offset = row_item(I0, ta, tb, aut);
+            cnts[i].items = row_item(I1, ta, tb, aut) - cnts[i].offset;
+            cnts[i].total = aut ? auto_pairs_in_rows(n_a, r0, r1)
+                                : (unsigned long long)(r1 - r0) * (unsigned long long)n_b;
+        }
+        total_items = 0;
+        for (const Cnt& c : cnts) total_items += c.items;
     }
     Segment segs[3];
     CullSeg cs[3];
@@ -2233,14 +2440,9 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
         const Prepared& B = k == 0 ? D : R;
         const long long ta = k == 2 ? tr : td, tb = k == 0 ? td : tr;
         segs[i] = make_segment(A, B, ta, tb, k != 1, item, counts + (size_t)k * K2, cnts[i].total);
-        std::memset(&cs[i], 0, sizeof(CullSeg));
-        cs[i].begin = item;
-        cs[i].n = cnts[i].items;
-        cs[i].ta = ta;
-        cs[i].tb = tb;
-        cs[i].is_auto = k != 1;
-        cs[i].ca = k == 2 ? caps_r : caps_d;
-        cs[i].cb = k == 0 ? caps_d : caps_r;
+        segs[i].n_items = cnts[i].items;
+        segs[i].item_offset = cnts[i].offset;
+        cs[i] = cull_seg(i, item);
         cs[i].list = (unsigned*)(m + off_lists) + item;
         item += cnts[i].items;
     }
@@ -2253,15 +2455,14 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
                                             cudaMemcpyHostToDevice, st));
             if (!rc) rc = check_cuda(cudaMemsetAsync(d_kept, 0, 3 * 8, st));
             if (!rc)
-                rc = launch_cull_batch(d_cull, n_segs, total_items,
-                                       edges[K] * (3.14159265358979323846 / 180.0), d_kept,
-                                       d_segs, n_kept, di.sm_count, st, stats);
+                rc = launch_cull_batch(d_cull, n_segs, total_items, theta_top, d_kept, d_segs,
+                                       n_kept, di.sm_count, st, stats);
         }
         const size_t smem = v->smem(K, tab.n_lut);
         int grid = 0;
         const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
-        if (!rc) rc = grid_for(v, smem, total_items, di.sm_count, want_per_sm, &grid);
-        if (!rc) {
+        if (!rc) rc = grid_for(v, smem, std::max(total_items, 1LL), di.sm_count, want_per_sm, &grid);
+        if (!rc && total_items > 0) {
             PairParams prm = make_params(v, tab, nullptr, d_segs, n_segs, 0, total_items, cursor,
                                          stats);
             if (cull) prm.n_items_dev = n_kept;
@@ -2458,6 +2659,7 @@ struct wtheta_plan {
     int dev = 0;
     int K = 0;
     int n_cats = 0;
+    int is_xyz = 0;                        // catalogues are SoA unit vectors, not RA/Dec
     wtheta::BinTable tab;
     const wtheta::Variant* v = nullptr;
     wtheta_tune tune = {};
@@ -2527,9 +2729,9 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
         P->n_pad[2 * m] = round_up(nd, T);
         P->n_pad[2 * m + 1] = round_up(nr, T);
         off[2 * m] = bytes;
-        bytes += (prepare_bytes(nd, P->n_pad[2 * m], 0) + 255) / 256 * 256;
+        bytes += (prepare_bytes(nd, P->n_pad[2 * m], P->is_xyz) + 255) / 256 * 256;
         off[2 * m + 1] = bytes;
-        bytes += (prepare_bytes(nr, P->n_pad[2 * m + 1], 0) + 255) / 256 * 256;
+        bytes += (prepare_bytes(nr, P->n_pad[2 * m + 1], P->is_xyz) + 255) / 256 * 256;
     }
     if (P->scratch) cudaFree(P->scratch);
     P->scratch = nullptr;
@@ -2539,10 +2741,10 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
     P->d_cursor = (unsigned long long*)base;
     P->prep.assign(2 * nc, Prepared());
     for (int m = 0; m < nc; ++m) {
-        rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], 0, 0, base + off[2 * m],
-                     sm_count, st, &P->prep[2 * m]);
+        rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], P->is_xyz, 0,
+                     base + off[2 * m], sm_count, st, &P->prep[2 * m]);
         if (!rc)
-            rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, 1,
+            rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], P->is_xyz, 1,
                          base + off[2 * m + 1], sm_count, st, &P->prep[2 * m + 1]);
         if (rc) return rc;
     }
@@ -2694,16 +2896,16 @@ static int plan_capture(wtheta_plan* P, const DeviceInfo& di) {
     const unsigned long long launches0 = g_launches.load();
     rc = check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     if (!rc) {
-        // re-prepare every catalogue from its current RA/Dec, then count
+        // re-prepare every catalogue from its current coordinates, then count
         unsigned char* base = (unsigned char*)P->scratch;
         for (int m = 0; m < P->n_cats && !rc; ++m) {
             Prepared a, b;
             const size_t off_a = (size_t)((const unsigned char*)P->prep[2 * m].p32 - base);
             const size_t off_b = (size_t)((const unsigned char*)P->prep[2 * m + 1].p32 - base);
-            rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], 0, 0, base + off_a,
-                         di.sm_count, cs, &a);
+            rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], P->is_xyz, 0,
+                         base + off_a, di.sm_count, cs, &a);
             if (!rc)
-                rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], 0, 1,
+                rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], P->is_xyz, 1,
                              base + off_b, di.sm_count, cs, &b);
         }
         if (!rc && P->cull) {
@@ -2765,9 +2967,10 @@ static void plan_release(wtheta_plan* P) {
     delete P;
 }
 
-static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, const double* edges, int K,
-                           const wtheta_tune* tune, cudaStream_t st, wtheta_plan** out) {
-    if (!out || !cats || n_cats < 1) return WTHETA_EINVAL;
+static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, int is_xyz,
+                           const double* edges, int K, const wtheta_tune* tune, cudaStream_t st,
+                           wtheta_plan** out) {
+    if (!out || !cats || n_cats < 1 || (is_xyz != 0 && is_xyz != 1)) return WTHETA_EINVAL;
     for (int m = 0; m < n_cats; ++m) {
         const wtheta_catalog_pair& c = cats[m];
         if (c.n_data < 2 || c.n_rand < 2 || !c.data || !c.rand) return WTHETA_EINVAL;
@@ -2781,6 +2984,7 @@ static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, const do
     wtheta_plan* P = new wtheta_plan();
     P->K = K;
     P->n_cats = n_cats;
+    P->is_xyz = is_xyz;
     P->cats.assign(cats, cats + n_cats);
     int rc = build_table(edges, K, &P->tab);
     if (!rc) {
@@ -2908,7 +3112,14 @@ int wtheta_count_xyz_noalloc(const double* a, int64_t n_a, const double* b, int6
 
 int wtheta_batch_plan(const wtheta_catalog_pair* cats, int32_t n_cats, const double* edges,
                       int32_t K, const wtheta_tune* tune, void* stream, wtheta_plan** plan) {
-    return batch_plan_impl(cats, n_cats, edges, K, tune, (cudaStream_t)stream, plan);
+    return batch_plan_impl(cats, n_cats, 0, edges, K, tune, (cudaStream_t)stream, plan);
+}
+
+int wtheta_batch_plan_ex(const wtheta_catalog_pair* cats, int32_t n_cats, int32_t coords_are_xyz,
+                         const double* edges, int32_t K, const wtheta_tune* tune, void* stream,
+                         wtheta_plan** plan) {
+    return batch_plan_impl(cats, n_cats, coords_are_xyz, edges, K, tune, (cudaStream_t)stream,
+                           plan);
 }
 
 int wtheta_batch_run(wtheta_plan* P, uint64_t* counts, void* stream) {
@@ -3018,6 +3229,15 @@ int wtheta_count_wtheta(const double* coords_d, int64_t n_d, const double* coord
     return count_wtheta_impl(coords_d, n_d, coords_r, n_r, coords_are_xyz, bin_edges_deg, n_bins,
                              (unsigned long long*)counts, tune, (unsigned long long*)stats,
                              (cudaStream_t)stream);
+}
+
+int wtheta_count_wtheta_shard(const double* coords_d, int64_t n_d, const double* coords_r,
+                              int64_t n_r, int32_t coords_are_xyz, const double* bin_edges_deg,
+                              int32_t n_bins, int32_t shard, int32_t n_shards, uint64_t* counts,
+                              const wtheta_tune* tune, uint64_t* stats, void* stream) {
+    return count_wtheta_impl(coords_d, n_d, coords_r, n_r, coords_are_xyz, bin_edges_deg, n_bins,
+                             (unsigned long long*)counts, tune, (unsigned long long*)stats,
+                             (cudaStream_t)stream, shard, n_shards);
 }
 
 int wtheta_correlate(const double* data, int64_t n_d, const double* rand, int64_t n_r,

@@ -282,6 +282,32 @@ int wtheta_shard_rows(int64_t n_a, int64_t n_b, int32_t is_auto, int32_t shard, 
     return WTHETA_OK;
 }
 
+int wtheta_shard_weights(const uint64_t* weights, int64_t n_rows, int32_t shard,
+                         int32_t n_shards, int64_t* row_begin, int64_t* row_end) {
+    if (!row_begin || !row_end || n_rows < 0 || (n_rows > 0 && !weights) || n_shards < 1 ||
+        shard < 0 || shard >= n_shards)
+        return WTHETA_EINVAL;
+    unsigned __int128 total = 0;
+    for (int64_t r = 0; r < n_rows; ++r) total += weights[r];
+    // boundary s: the smallest row r whose prefix weight reaches s / n_shards of
+    // the total (rows split evenly by number when every weight is zero)
+    auto boundary = [&](int s) -> long long {
+        if (s <= 0) return 0;
+        if (s >= n_shards) return n_rows;
+        if (total == 0) return (long long)((__int128)n_rows * s / n_shards);
+        const unsigned __int128 target = total * (unsigned)s;  // compared with prefix * n_shards
+        unsigned __int128 prefix = 0;
+        for (int64_t r = 0; r < n_rows; ++r) {
+            if (prefix * (unsigned)n_shards >= target) return r;
+            prefix += weights[r];
+        }
+        return n_rows;
+    };
+    *row_begin = boundary(shard);
+    *row_end = boundary(shard + 1);
+    return WTHETA_OK;
+}
+
 int wtheta_ls(const uint64_t* DD, const uint64_t* DR, const uint64_t* RR, int64_t nd,
               int64_t nr, int32_t K, double* w) {
     if (!DD || !DR || !RR || !w || K < 1 || K > kMaxBins || nd < 2 || nr < 2)

@@ -71,6 +71,7 @@ struct TileCap {
 // items in the full work table, its tiles' caps, and the list of kept items.
 struct CullSeg {
     long long begin, n;
+    long long offset;        // the count's item that index 0 of this range is (a shard's rows)
     const TileCap* ca;
     const TileCap* cb;
     long long ta, tb;

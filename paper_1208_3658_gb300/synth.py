@@ -217,23 +217,32 @@ class Mock:
     rand: np.ndarray
 
 
+def batch_sizes(seed: int = 1, n_mocks: int = 256, n_lo: int = 20_000,
+                n_hi: int = 400_000) -> np.ndarray:
+    """Data sizes of the batch workload's mocks, log-uniform in [n_lo, n_hi]."""
+    rs = rng_for(seed, "batch", "sizes")
+    return np.rint(np.exp(rs.uniform(math.log(n_lo), math.log(n_hi), n_mocks))).astype(np.int64)
+
+
+def batch_mock(seed: int, m: int, n_mocks: int = 256, n_lo: int = 20_000,
+               n_hi: int = 400_000) -> Mock:
+    """Mock m of batch_mocks alone (same streams, same points)."""
+    n = int(batch_sizes(seed, n_mocks, n_lo, n_hi)[m])
+    rp = rng_for(seed, "batch", "patch")
+    ra0 = rp.uniform(0.0, 360.0, n_mocks)
+    dec0 = rp.uniform(-60.0, 45.0, n_mocks)
+    fp = Patch(float(ra0[m]), 15.0, float(dec0[m]), float(dec0[m]) + 15.0)
+    d = clustered(fp, n, math.ceil(n / 50), 3.0, seed, "batch", "data", m)
+    r = uniform(fp, 2 * n, seed, "batch", "random", m)
+    return Mock(d, r)
+
+
 def batch_mocks(seed: int = 1, n_mocks: int = 256, n_lo: int = 20_000,
                 n_hi: int = 400_000) -> Tuple[List[Mock], Tuple[float, float, int]]:
     """256 mocks, sizes log-uniform in [20k, 400k], each clustered (n/50
     centres, sigma 3') in its own 15x15 deg patch with 2x uniform randoms;
     16 log bins 1'-5 deg."""
-    rs = rng_for(seed, "batch", "sizes")
-    sizes = np.rint(np.exp(rs.uniform(math.log(n_lo), math.log(n_hi), n_mocks))).astype(np.int64)
-    rp = rng_for(seed, "batch", "patch")
-    ra0 = rp.uniform(0.0, 360.0, n_mocks)
-    dec0 = rp.uniform(-60.0, 45.0, n_mocks)
-    mocks = []
-    for m in range(n_mocks):
-        fp = Patch(float(ra0[m]), 15.0, float(dec0[m]), float(dec0[m]) + 15.0)
-        n = int(sizes[m])
-        d = clustered(fp, n, math.ceil(n / 50), 3.0, seed, "batch", "data", m)
-        r = uniform(fp, 2 * n, seed, "batch", "random", m)
-        mocks.append(Mock(d, r))
+    mocks = [batch_mock(seed, m, n_mocks, n_lo, n_hi) for m in range(n_mocks)]
     return mocks, (1.0 * ARCMIN, 5.0, 16)
 
 
@@ -247,12 +256,7 @@ class Request:
     rand2: np.ndarray | None = None
 
 
-def serve_requests(seed: int = 1, n_requests: int = 2000, n_lo: int = 1_000,
-                   n_hi: int = 2_000_000, rate_hz: float = 1.0,
-                   auto_frac: float = 0.7) -> Tuple[List[Request], Tuple[float, float, int]]:
-    """Poisson-arrival w(theta) requests, sizes log-uniform in [n_lo, n_hi] with
-    1:1 randoms, 70% auto / 30% cross, each in a 15x15 deg patch clustered as
-    the small workload; 24 log bins 1'-10 deg."""
+def _serve_plan(seed, n_requests, n_lo, n_hi, rate_hz, auto_frac):
     ra = rng_for(seed, "serve", "arrivals")
     gaps = ra.exponential(1.0 / rate_hz, n_requests)
     t = np.cumsum(gaps) - gaps[0]
@@ -262,19 +266,41 @@ def serve_requests(seed: int = 1, n_requests: int = 2000, n_lo: int = 1_000,
     rp = rng_for(seed, "serve", "patch")
     ra0 = rp.uniform(0.0, 360.0, n_requests)
     dec0 = rp.uniform(-60.0, 45.0, n_requests)
-    reqs = []
-    for q in range(n_requests):
-        fp = Patch(float(ra0[q]), 15.0, float(dec0[q]), float(dec0[q]) + 15.0)
-        n = int(sizes[q])
-        nc = max(1, math.ceil(n / 50))
-        d = clustered(fp, n, nc, 3.0, seed, "serve", "data", q)
-        r = uniform(fp, n, seed, "serve", "random", q)
-        if kinds[q]:
-            reqs.append(Request(float(t[q]), "auto", d, r))
-        else:
-            d2 = clustered(fp, n, nc, 3.0, seed, "serve", "data2", q)
-            r2 = uniform(fp, n, seed, "serve", "random2", q)
-            reqs.append(Request(float(t[q]), "cross", d, r, d2, r2))
+    return t, sizes, kinds, ra0, dec0
+
+
+def serve_sizes(seed: int = 1, n_requests: int = 2000, n_lo: int = 1_000,
+                n_hi: int = 2_000_000, auto_frac: float = 0.7):
+    """(sizes, is_auto) of the serve workload's requests."""
+    _, sizes, kinds, _, _ = _serve_plan(seed, n_requests, n_lo, n_hi, 1.0, auto_frac)
+    return sizes, kinds
+
+
+def serve_request(seed: int, q: int, n_requests: int = 2000, n_lo: int = 1_000,
+                  n_hi: int = 2_000_000, rate_hz: float = 1.0,
+                  auto_frac: float = 0.7) -> Request:
+    """Request q of serve_requests alone (same streams, same points)."""
+    t, sizes, kinds, ra0, dec0 = _serve_plan(seed, n_requests, n_lo, n_hi, rate_hz, auto_frac)
+    fp = Patch(float(ra0[q]), 15.0, float(dec0[q]), float(dec0[q]) + 15.0)
+    n = int(sizes[q])
+    nc = max(1, math.ceil(n / 50))
+    d = clustered(fp, n, nc, 3.0, seed, "serve", "data", q)
+    r = uniform(fp, n, seed, "serve", "random", q)
+    if kinds[q]:
+        return Request(float(t[q]), "auto", d, r)
+    d2 = clustered(fp, n, nc, 3.0, seed, "serve", "data2", q)
+    r2 = uniform(fp, n, seed, "serve", "random2", q)
+    return Request(float(t[q]), "cross", d, r, d2, r2)
+
+
+def serve_requests(seed: int = 1, n_requests: int = 2000, n_lo: int = 1_000,
+                   n_hi: int = 2_000_000, rate_hz: float = 1.0,
+                   auto_frac: float = 0.7) -> Tuple[List[Request], Tuple[float, float, int]]:
+    """Poisson-arrival w(theta) requests, sizes log-uniform in [n_lo, n_hi] with
+    1:1 randoms, 70% auto / 30% cross, each in a 15x15 deg patch clustered as
+    the small workload; 24 log bins 1'-10 deg."""
+    reqs = [serve_request(seed, q, n_requests, n_lo, n_hi, rate_hz, auto_frac)
+            for q in range(n_requests)]
     return reqs, (1.0 * ARCMIN, 10.0, 24)
 
 

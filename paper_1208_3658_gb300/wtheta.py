@@ -128,6 +128,9 @@ def lib() -> ctypes.CDLL:
             L.wtheta_batch_plan.argtypes = [ctypes.POINTER(wtheta_catalog_pair), i32, dp, i32,
                                             ctypes.POINTER(wtheta_tune), vp,
                                             ctypes.POINTER(ctypes.c_void_p)]
+            L.wtheta_batch_plan_ex.argtypes = [ctypes.POINTER(wtheta_catalog_pair), i32, i32, dp,
+                                               i32, ctypes.POINTER(wtheta_tune), vp,
+                                               ctypes.POINTER(ctypes.c_void_p)]
             L.wtheta_batch_run.argtypes = [vp, vp, vp]
             L.wtheta_batch_info.argtypes = [vp, ctypes.POINTER(wtheta_batch_info_t)]
             L.wtheta_batch_free.argtypes = [vp]
@@ -148,6 +151,11 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int64)]
             L.wtheta_count_shard.argtypes = [vp, i64, vp, i64, dp, i32, i32, i32, i32, vp, vp]
+            L.wtheta_count_wtheta_shard.argtypes = [vp, i64, vp, i64, i32, dp, i32, i32, i32, vp,
+                                                    ctypes.POINTER(wtheta_tune), vp, vp]
+            L.wtheta_shard_weights.argtypes = [u64p, i64, i32, i32,
+                                               ctypes.POINTER(ctypes.c_int64),
+                                               ctypes.POINTER(ctypes.c_int64)]
             L.wtheta_kernel_launches.argtypes = []
             L.wtheta_kernel_launches.restype = ctypes.c_uint64
             _lib = L
@@ -321,19 +329,27 @@ class BatchPlan:
             self.handle = None
 
 
-def wtheta_batch_plan(cats, edges_deg, tune: dict | None = None, stream=None) -> BatchPlan:
-    """cats: list of (data, rand) CUDA float64 tensors of interleaved RA/Dec."""
+def wtheta_batch_plan(cats, edges_deg, tune: dict | None = None, stream=None,
+                      coords_are_xyz: bool = False) -> BatchPlan:
+    """cats: list of (data, rand) CUDA float64 tensors: interleaved RA/Dec, or
+    SoA (3, n) unit vectors when coords_are_xyz (wtheta_batch_plan_ex)."""
     e, ep = _host_f64(edges_deg)
+    per = 3 if coords_are_xyz else 2
     arr = (wtheta_catalog_pair * len(cats))()
     keep = []
     for i, (d, r) in enumerate(cats):
-        arr[i] = wtheta_catalog_pair(_dev_ptr(d), _n_points(d, 2), _dev_ptr(r), _n_points(r, 2))
+        arr[i] = wtheta_catalog_pair(_dev_ptr(d), _n_points(d, per), _dev_ptr(r),
+                                     _n_points(r, per))
         keep += [d, r]
     t = _tune_struct(tune)
     h = ctypes.c_void_p()
-    _check(lib().wtheta_batch_plan(arr, len(cats), ep, len(e) - 1,
-                                   ctypes.byref(t) if t is not None else None, _stream(stream),
-                                   ctypes.byref(h)), "wtheta_batch_plan")
+    tp = ctypes.byref(t) if t is not None else None
+    if coords_are_xyz:
+        _check(lib().wtheta_batch_plan_ex(arr, len(cats), 1, ep, len(e) - 1, tp, _stream(stream),
+                                          ctypes.byref(h)), "wtheta_batch_plan_ex")
+    else:
+        _check(lib().wtheta_batch_plan(arr, len(cats), ep, len(e) - 1, tp, _stream(stream),
+                                       ctypes.byref(h)), "wtheta_batch_plan")
     return BatchPlan(h, keep, len(cats), len(e) - 1)
 
 
@@ -479,6 +495,32 @@ def wtheta_count_wtheta(coords_d, coords_r, coords_are_xyz: bool, edges_deg, cou
                                      1 if coords_are_xyz else 0, ep, len(e) - 1, _dev_ptr(counts),
                                      ctypes.byref(t) if t is not None else None, _dev_ptr(stats),
                                      _stream(stream)), "wtheta_count_wtheta")
+
+
+def wtheta_count_wtheta_shard(coords_d, coords_r, coords_are_xyz: bool, edges_deg, shard: int,
+                              n_shards: int, counts, tune: dict | None = None, stats=None,
+                              stream=None):
+    """Shard `shard` of n_shards of one w(theta): DD, DR, RR of the pairs whose
+    first point lies in the shard's tile rows (balanced by kept tile pairs)."""
+    e, ep = _host_f64(edges_deg)
+    per = 3 if coords_are_xyz else 2
+    t = _tune_struct(tune)
+    _check(lib().wtheta_count_wtheta_shard(_dev_ptr(coords_d), _n_points(coords_d, per),
+                                           _dev_ptr(coords_r), _n_points(coords_r, per),
+                                           1 if coords_are_xyz else 0, ep, len(e) - 1, shard,
+                                           n_shards, _dev_ptr(counts),
+                                           ctypes.byref(t) if t is not None else None,
+                                           _dev_ptr(stats), _stream(stream)),
+           "wtheta_count_wtheta_shard")
+
+
+def wtheta_shard_weights(weights, shard: int, n_shards: int):
+    """[row_begin, row_end) of shard among n_shards contiguous weighted ranges."""
+    w, wp = _host_u64(weights)
+    r0, r1 = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().wtheta_shard_weights(wp, len(w), shard, n_shards, ctypes.byref(r0),
+                                      ctypes.byref(r1)), "wtheta_shard_weights")
+    return int(r0.value), int(r1.value)
 
 
 def wtheta_radec_to_xyz(ra_dec, xyz, stream=None):

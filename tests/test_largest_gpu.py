@@ -10,8 +10,9 @@ what holds at any size and by samples the oracle can compute:
     (cos t1 - cos t2)/2, independently of the other pairs), within 5 sigma;
   - 400 sampled data rows against all 10M randoms, bit-identical to the
     oracle on its own unit vectors;
-  - a seeded 200k + 200k subsample: DD, DR, RR against the oracle (P2: the
-    device converts RA/Dec; pairs within a few ulps of an edge may differ).
+  - a seeded 200k + 200k subsample: DD, DR, RR against the oracle, P1 on the
+    oracle's unit vectors (zero tolerance) and P2 from RA/Dec (the device
+    converts; pairs within a few ulps of an edge may differ).
 """
 import numpy as np
 import pytest
@@ -77,20 +78,31 @@ def test_full_size_sampled_rows_against_oracle(W, wl):
 
 
 def test_subsample_200k_against_oracle(W, wl):
+    """DD, DR and RR of a seeded 200k + 200k subsample: P1 through
+    wtheta_count_wtheta on the oracle's own unit vectors (library defaults:
+    far tile pairs skipped, spans settled), every slot bit-identical; P2
+    through wtheta_count from RA/Dec (the device converts; only pairs within
+    a few ulps of an edge may move)."""
     e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
     rng = np.random.default_rng(12)
     sd = np.sort(rng.choice(wl.n_d, 200_000, replace=False))
     sr = np.sort(rng.choice(wl.n_r, 200_000, replace=False))
     d = wl.data.reshape(-1, 2)[sd].reshape(-1)
     r = wl.rand.reshape(-1, 2)[sr].reshape(-1)
-    for a, b, auto in [(d, None, True), (d, r, False), (r, None, True)]:
+    D, R = O.radec_to_xyz(d), O.radec_to_xyz(r)
+    K = wl.n_bins
+    c = torch.zeros((3, K + 2), dtype=torch.int64, device="cuda")
+    W.wtheta_count_wtheta(torch.from_numpy(D).cuda(), torch.from_numpy(R).cuda(), True, e, c)
+    torch.cuda.synchronize()
+    p1 = c.cpu().numpy().astype(np.uint64)
+    for k, (a, b, A, B, auto) in enumerate([(d, None, D, None, True), (d, r, D, R, False),
+                                            (r, None, R, None, True)]):
+        want = O.count_xyz(A, B, e, auto)
+        assert np.array_equal(p1[k], want), k
         got = _count(W, a, b, e, auto)
-        want = O.count(a, b, e, auto)
         assert int(got.sum()) == int(want.sum())
         if np.array_equal(got, want):
             continue
         # P2: only pairs within a few ulps of an edge may move
-        A = O.radec_to_xyz(a)
-        B = None if auto else O.radec_to_xyz(b)
         amb = O.count_ambiguous_xyz(A, B, e, auto)
         assert np.abs(got.astype(np.int64) - want.astype(np.int64)).sum() <= 2 * amb

@@ -296,6 +296,43 @@ def test_shards_sum_to_the_whole_count(W, is_auto):
         assert torch.equal(acc, whole), S
 
 
+def test_wtheta_shards_sum_to_the_oracle_and_balance_work(W):
+    """wtheta_count_wtheta_shard: every shard's 3 (K+2) counts are exact for
+    the pairs of its tile rows (their slots sum to its pairs), the shards add
+    up, slot by slot, to the oracle's whole DD, DR and RR (P1: the oracle's
+    unit vectors), and shards of a clustered survey get similar numbers of
+    kept tile pairs (the split's weights) -- Sec. 5's division of the data set
+    over independent GPUs, one sum-reduction combining them."""
+    wl = synth.survey(n=60_000)
+    e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
+    D, R = O.radec_to_xyz(wl.data), O.radec_to_xyz(wl.rand)
+    want = [O.count_xyz(D, None, e, True), O.count_xyz(D, R, e, False),
+            O.count_xyz(R, None, e, True)]
+    d, r = dev(D), dev(R)
+    K = wl.n_bins
+    for S in (1, 2, 3, 5, 200):
+        acc = np.zeros((3, K + 2), np.uint64)
+        tiles = []
+        for s in range(S):
+            c = torch.zeros((3, K + 2), dtype=torch.int64, device="cuda")
+            st = torch.zeros(W.NSTATS, dtype=torch.int64, device="cuda")
+            W.wtheta_count_wtheta_shard(d, r, True, e, s, S, c, stats=st)
+            torch.cuda.synchronize()
+            acc += c.cpu().numpy().astype(np.uint64)
+            tiles.append(int(st.cpu().numpy()[W.STAT_TILES]))
+        for k in range(3):
+            assert np.array_equal(acc[k], want[k]), (S, k)
+        if 1 < S <= 5:
+            # equal work: each count's share is within one tile row's kept tile
+            # pairs (at most a row's tiles, 512-point tiles here) of an even split
+            row = -(-max(wl.n_d, wl.n_r) // 512)
+            assert max(tiles) - min(tiles) <= 2 * 3 * row, (S, tiles)
+            assert min(tiles) > 0.5 * sum(tiles) / S, (S, tiles)
+    with pytest.raises(W.WthetaError):
+        W.wtheta_count_wtheta_shard(d, r, True, e, 3, 3, torch.zeros((3, K + 2), dtype=torch.int64,
+                                                                   device="cuda"))
+
+
 @pytest.mark.parametrize("case", ["survey_200k", "fullsky_150k", "small"])
 def test_skipping_far_tile_pairs_is_exact(W, case):
     """Counts with tile pairs skipped by their bounding caps equal counts with
