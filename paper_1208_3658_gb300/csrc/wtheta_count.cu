@@ -322,94 +322,6 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
     }
 }
 
-// The whole spatial order of a small catalogue (n <= kSmallSort) in one
-// block: the keys of k_sort_keys, then the same stable LSD radix sort (four
-// 8-bit passes; in each pass rounds of 1024 keys, ranked inside a warp by
-// __match_any_sync and across warps by per-warp digit counts) with keys and
-// 16-bit indices in shared memory.  One launch instead of thirteen.
-constexpr int kSmallSort = 12288;
-constexpr int kSmallSortThreads = 1024;
-constexpr size_t kSmallSortSmem =
-    (size_t)kSmallSort * (2 * 4 + 2 * 2) + (size_t)(kSmallSortThreads / 32) * 256 * 2 + 256 * 4;
-
-__global__ void __launch_bounds__(kSmallSortThreads) k_sort_small(const double* __restrict__ xyz,
-                                                                  long long stride, int n,
-                                                                  int check,
-                                                                  unsigned* __restrict__ order) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    unsigned* key0 = reinterpret_cast<unsigned*>(sm);
-    unsigned* key1 = key0 + kSmallSort;
-    unsigned short* idx0 = reinterpret_cast<unsigned short*>(key1 + kSmallSort);
-    unsigned short* idx1 = idx0 + kSmallSort;
-    unsigned short* wcnt = idx1 + kSmallSort;                       // [warp][digit]
-    unsigned* base = reinterpret_cast<unsigned*>(wcnt + (kSmallSortThreads / 32) * 256);
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    constexpr int NW = kSmallSortThreads / 32;
-    for (int i = t; i < n; i += kSmallSortThreads) {
-        const double x = xyz[i], y = xyz[stride + i], z = xyz[2 * stride + i];
-        if (check) check_unit(x, y, z);
-        key0[i] = cell_key(x, y, z, kSortLevel);
-        idx0[i] = (unsigned short)i;
-    }
-    unsigned *kin = key0, *kout = key1;
-    unsigned short *iin = idx0, *iout = idx1;
-    for (int pass = 0; pass < 4; ++pass) {
-        const int shift = 8 * pass;
-        if (t < 256) base[t] = 0;
-        __syncthreads();
-        // digit totals, then their exclusive prefix (thread d owns digit d)
-        for (int i = t; i < n; i += kSmallSortThreads) atomicAdd(&base[(kin[i] >> shift) & 255u], 1u);
-        __syncthreads();
-        if (w == 0) {
-            unsigned run = 0;
-            for (int d0 = 0; d0 < 256; d0 += 32) {
-                const unsigned c = base[d0 + lane];
-                unsigned incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += v;
-                }
-                base[d0 + lane] = run + incl - c;
-                run += __shfl_sync(0xffffffffu, incl, 31);
-            }
-        }
-        __syncthreads();
-        for (int r0 = 0; r0 < n; r0 += kSmallSortThreads) {
-            for (int q = t; q < NW * 256; q += kSmallSortThreads) wcnt[q] = 0;
-            __syncthreads();
-            const int i = r0 + t;
-            const bool valid = i < n;
-            const unsigned k = valid ? kin[i] : 0u;
-            const unsigned d = valid ? (k >> shift) & 255u : 256u;
-            const unsigned peers = __match_any_sync(0xffffffffu, d);
-            const unsigned rank = __popc(peers & ((1u << lane) - 1u));
-            if (valid && rank == 0) wcnt[w * 256 + d] = (unsigned short)__popc(peers);
-            __syncthreads();
-            if (t < 256) {
-                // warp q's keys of digit t go from wcnt[q][t] on (positions < 2^16)
-                unsigned acc = base[t];
-                for (int q = 0; q < NW; ++q) {
-                    const unsigned c = wcnt[q * 256 + t];
-                    wcnt[q * 256 + t] = (unsigned short)acc;
-                    acc += c;
-                }
-                base[t] = acc;
-            }
-            __syncthreads();
-            if (valid) {
-                const unsigned pos = (unsigned)wcnt[w * 256 + d] + rank;
-                kout[pos] = k;
-                iout[pos] = iin[i];
-            }
-            __syncthreads();
-        }
-        unsigned* tk = kin; kin = kout; kout = tk;
-        unsigned short* ti = iin; iin = iout; iout = ti;
-    }
-    for (int i = t; i < n; i += kSmallSortThreads) order[i] = iin[i];
-}
-
 // Exclusive prefix sum in place (one block of 1024).
 __global__ void __launch_bounds__(1024) k_exclusive_scan(unsigned* __restrict__ a, int n) {
     __shared__ unsigned warp_sum[32];
@@ -1968,17 +1880,6 @@ int spatial_order(const double* x64, long long stride, long long n, int check,
     *order = idx[0];
     if (sorted_labels) *sorted_labels = nullptr;
     if (n <= 0) return WTHETA_OK;
-    if (!labels && n <= kSmallSort) {
-        // small catalogue: the whole sort in one block
-        static const bool attr_ok =
-            cudaFuncSetAttribute((const void*)k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmallSortSmem) == cudaSuccess;
-        if (!attr_ok) return WTHETA_ECUDA;
-        k_sort_small<<<1, kSmallSortThreads, kSmallSortSmem, st>>>(x64, stride, (int)n, check,
-                                                                   idx[0]);
-        count_launch();
-        return check_cuda(cudaGetLastError());
-    }
     k_sort_keys<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, check, key[0], idx[0]);
     count_launch();
     for (int pass = 0; pass < 4; ++pass) {
