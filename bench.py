@@ -69,13 +69,21 @@ def parse_args():
     ap.add_argument("--replicas", action="store_true",
                     help="N > 1: independent replicas of the workload (weak scaling) instead "
                          "of one w(theta) sharded over the ranks")
+    ap.add_argument("--bins", type=int, default=0,
+                    help="number of log bins over the workload's range (default: the "
+                         "workload's own; e.g. 256 for the large-K span path)")
     ap.add_argument("--n", type=int, default=0,
                     help="points per catalogue (same shape, smaller: profiling cases)")
     return ap.parse_args()
 
 
-def make_workload(name, seed, n=0):
+def make_workload(name, seed, n=0, bins=0):
     from paper_1208_3658_gb300 import synth
+    if bins:
+        wl, desc = make_workload(name, seed, n)
+        wl.n_bins = bins
+        return wl, desc.replace("%d log bins" % {"small": 16, "survey": 32, "largest": 64}.get(
+            name, 0), "%d log bins" % bins) + (" (%d log bins)" % bins if n else "")
     if n:
         wl = {"small": synth.small, "survey": synth.survey, "largest": synth.largest}[name](
             seed=seed, n=n)
@@ -242,7 +250,8 @@ def run_ours(args, rank, world, dist):
     dev = torch.device("cuda", local)
     props = torch.cuda.get_device_properties(dev)
     sharded = world > 1 and not args.replicas and not args.separate_counts
-    wl, desc = make_workload(args.workload, seed=1 if sharded else 1 + rank, n=args.n)
+    wl, desc = make_workload(args.workload, seed=1 if sharded else 1 + rank, n=args.n,
+                             bins=args.bins)
     e = W.wtheta_edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
     K = wl.n_bins
     d_data = torch.from_numpy(wl.data).to(dev)
@@ -818,7 +827,7 @@ def run_reference(args, rank, world):
     """The CPU oracle on the host cores, each step a bounded sample (data rows
     against all randoms) of the same workload."""
     from oracle import oracle as O
-    wl, desc = make_workload(args.workload, seed=1, n=args.n)
+    wl, desc = make_workload(args.workload, seed=1, n=args.n, bins=args.bins)
     e = O.edges(wl.lo_deg, wl.hi_deg, wl.n_bins)
     cal = oracle_sample_rate(wl, e, target_s=4.0)
     import numpy as np

@@ -173,7 +173,9 @@ typedef struct wtheta_tune {
     int32_t points_per_thread; /* A points held in registers per thread: 8 or 16 */
     int32_t hist_mode;         /* 1: private per-thread histograms, plain add;
                                   2: per-warp histograms, warp-aggregated atomics;
-                                  3: private per-thread histograms, shared atomic add */
+                                  3: private per-thread histograms, shared atomic add;
+                                  4: per-warp histograms, shared atomic add (lanes on
+                                     one word merged by the hardware)              */
     int32_t j_per_screen;      /* B points per screening test: 1 or 2          */
     int32_t deferred;          /* 1: bin in-range pairs as they are screened;
                                   2: note screened steps, recompute and bin after */

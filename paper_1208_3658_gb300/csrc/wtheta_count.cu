@@ -364,19 +364,20 @@ __global__ void k_gather_points(const double* __restrict__ xyz, long long stride
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
          i += (long long)gridDim.x * blockDim.x) {
         double x, y, z;
+        float4 q;
         if (i < n) {
             const long long j = order[i];
             x = xyz[j];
             y = xyz[stride + j];
             z = xyz[2 * stride + j];
-            p32[i] = point32(x, y, z, j);
+            q = point32(x, y, z, j);
         } else {
-            const float4 q = sentinel32(tag, i - n);
-            p32[i] = q;
+            q = sentinel32(tag, i - n);
             x = q.x;
             y = q.y;
             z = q.z;
         }
+        p32[i] = q;
         s64[i] = x;
         s64[n_pad + i] = y;
         s64[2 * n_pad + i] = z;
@@ -727,9 +728,14 @@ __device__ __forceinline__ unsigned recheck_slot(const Segment& S, long long ia,
             return (unsigned)hint + 1u;
         }
     }
-    unsigned k = 0;
-    while (k <= (unsigned)K && lds_f64(c64 + 8u * k) <= s) ++k;
-    return k;  // K+1 = overflow
+    // the number of edges at or below s, by bisection (K+1 = overflow)
+    unsigned lo = 0, hi = (unsigned)K + 1;
+    while (lo < hi) {
+        const unsigned mid = (lo + hi) >> 1;
+        if (lds_f64(c64 + 8u * mid) <= s) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 template <int NT, int R, int JU, int HM, int DEF>
@@ -737,7 +743,13 @@ struct PairKernel {
     static constexpr int TA = NT * R;   // A points per tile
     static constexpr int TB = NT * R;   // B points per tile (equal: auto needs square tiles)
     static constexpr int NW = NT / 32;
-    static constexpr int HCOLS = HM == kHistWarp ? NW : NT;
+    // columns of the private histograms (one per thread or per warp) and the
+    // words from one slot's row to the next: per-warp columns updated by
+    // shared reductions (kHistWarpRed) take an odd stride, so that lanes adding
+    // to different rows of their warp's column hit different banks
+    static constexpr int HCOLS = (HM == kHistWarp || HM == kHistWarpRed) ? NW : NT;
+    static constexpr int HSTRIDE = HM == kHistWarpRed ? (NW | 1) : HCOLS;
+    static constexpr unsigned ROWB = 4u * HSTRIDE;
 
     static size_t smem_bytes(int K, int n_lut) {
         size_t b = (size_t)TB * 24;             // B tile: {-x,-x,-y,-y} + {-z,-z}
@@ -745,20 +757,20 @@ struct PairKernel {
         b += (size_t)n_lut * 16;                // screening table
         b += (size_t)(K + 2) * 8;               // FP64 edges (+ pad)
         b += (size_t)(K + 2) * 8;               // guard band of every edge
-        b += (size_t)(K + 2) * HCOLS * 4;       // histograms, row K+1 a trash row
+        b += (size_t)(K + 2) * ROWB;            // histograms, row K+1 a trash row
         return b;
     }
 };
 
-template <int NT, int HCOLS>
+template <int NT, int HCOLS, int HSTRIDE = HCOLS>
 __device__ __forceinline__ void flush_hist(unsigned* hist, int K,
                                            unsigned long long* __restrict__ counts) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int b = warp; b <= K + 1; b += NT / 32) {
         unsigned long long sum = 0;
         for (int q = lane; q < HCOLS; q += 32) {
-            sum += hist[b * HCOLS + q];
-            hist[b * HCOLS + q] = 0;
+            sum += hist[b * HSTRIDE + q];
+            hist[b * HSTRIDE + q] = 0;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -827,7 +839,7 @@ __device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsign
             hist_add<HM>(col + e.w, 0xFFFFFFFFu);  // -1
             if (hint_v < 0) {
                 hint_v = v;
-                hint = e.w == e.z + row_bytes ? (int)(e.z >> (__ffs(row_bytes) - 1)) : -1;
+                hint = e.w == e.z + row_bytes ? (int)(e.z / row_bytes) : -1;
             }
         }
     }
@@ -949,10 +961,10 @@ __device__ __forceinline__ float4 group_cap(const f2_t (&ax)[R / 2], const f2_t 
 //      edge's guard band;
 //   3  slots k, k+1, k+2, split by edges k and k+1: two comparisons per pair;
 //   2  anything else: bin pair by pair.
-// rlo is a byte offset of a slot's row, slot << row_shift; a span wholly
+// rlo is a byte offset of a slot's row, slot * row_bytes; a span wholly
 // above h_top (the top edge's band) is the overflow row trash at once.
 __device__ __forceinline__ int span_class(float4 ga, float4 gb, unsigned lut, int shift, int base,
-                                          int top_idx, int row_shift, unsigned& rlo,
+                                          int top_idx, unsigned row_bytes, unsigned& rlo,
                                           unsigned h_top, unsigned trash) {
     const float dx = ga.x - gb.x, dy = ga.y - gb.y, dz = ga.z - gb.z;
     const float dc = sqrtf(dx * dx + dy * dy + dz * dz);
@@ -972,8 +984,8 @@ __device__ __forceinline__ int span_class(float4 ga, float4 gb, unsigned lut, in
     rlo = bl < el.x ? el.z : el.w;
     const unsigned rhi = bh < eh.x ? eh.z : eh.w;
     if (rlo == rhi) return 0;
-    if (rhi == rlo + (1u << row_shift)) return 1;
-    if (rhi == rlo + (2u << row_shift)) return 3;
+    if (rhi == rlo + row_bytes) return 1;
+    if (rhi == rlo + 2u * row_bytes) return 3;
     return 2;
 }
 
@@ -1051,16 +1063,15 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
                                           int j_begin, int j_end,
                                           unsigned long long& n_recheck) {
     using PK = PairKernel<NT, R, JU, HM, DEF>;
-    constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
+    constexpr int TA = PK::TA, TB = PK::TB;
     constexpr int NV = JU * R;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned h_top = p.tab.h_top;
     const float hf = __uint_as_float(h_top);
     const int shift = p.tab.shift, base = p.tab.base, K = p.tab.K, top_idx = p.tab.n_lut - 1;
-    const unsigned row_bytes = HCOLS * 4u;
-    constexpr int row_shift = ilog2(HCOLS * 4);
-    static_assert((1 << row_shift) == HCOLS * 4, "rows are a power of two bytes");
-    const unsigned col = hist + 4u * (unsigned)(HM == kHistWarp ? warp : tid);
+    constexpr unsigned row_bytes = PK::ROWB;
+    const unsigned col =
+        hist + 4u * (unsigned)((HM == kHistWarp || HM == kHistWarpRed) ? warp : tid);
     const long long a0 = I * TA + a_first, b0 = J * TB;
 
     if (DEF) {
@@ -1188,7 +1199,7 @@ __device__ __forceinline__ void exact_chunk(int c0, int rot, int t0, int ts, int
                                             const PairParams& p, const Segment& S,
                                             unsigned& n_recheck) {
     using PK = PairKernel<NT, R, JU, HM, 0>;
-    constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
+    constexpr int TA = PK::TA, TB = PK::TB;
     constexpr int NV = R;  // one B point per step: fewer live values
     const float hf = __uint_as_float(p.tab.h_top);
     const int shift = p.tab.shift, base = p.tab.base, top_idx = p.tab.n_lut - 1;
@@ -1203,7 +1214,7 @@ __device__ __forceinline__ void exact_chunk(int c0, int rot, int t0, int ts, int
             chords<NT, R, 1, false>(s2, bxy, bz, ax, ay, az, j, 0);
             const long long a0 = lds_s64(sIJ) * TA + a_first;
             const long long b0 = lds_s64(sIJ + 8u) * TB;
-            recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, HCOLS * 4u,
+            recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, PK::ROWB,
                                                p.tab.K, S, a0, b0 + j, sC, n_recheck);
         }
     }
@@ -1298,12 +1309,10 @@ __device__ __forceinline__ void span_part(int T, unsigned job, int t0, int ts, u
 template <int NT, int R, int JU, int HM>
 __device__ __forceinline__ bool span_settle(int T, unsigned job, unsigned band, unsigned col,
                                             unsigned neg1, unsigned neg2, float mb1, float mb2) {
-    constexpr int HCOLS = PairKernel<NT, R, JU, HM, 0>::HCOLS;
-    constexpr int row_shift = ilog2(HCOLS * 4);
     constexpr unsigned NP = (unsigned)(R * kChunk);
-    constexpr unsigned row_bytes = HCOLS * 4u;
+    constexpr unsigned row_bytes = PairKernel<NT, R, JU, HM, 0>::ROWB;
     const unsigned slot = (job >> 16) & 0x3FFFu;
-    const unsigned rlo = slot << row_shift;
+    const unsigned rlo = slot * row_bytes;
     float G, G2 = 0.f;
     edge_mid(band, slot, G);
     if (mb1 <= G) return false;
@@ -1347,15 +1356,15 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
                                           const PairParams& p, const Segment& S, bool diag,
                                           unsigned stat) {
     using PK = PairKernel<NT, R, JU, HM, 0>;
-    constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
+    constexpr int TA = PK::TA, TB = PK::TB;
     constexpr int NW = NT / 32, SA = 32 * R, UPS = 4, UB = TB / UPS, CPU = UB / kChunk;
-    constexpr int row_shift = ilog2(HCOLS * 4);
+    constexpr unsigned row_bytes = PK::ROWB;
     constexpr unsigned NP = (unsigned)(R * kChunk);
     static_assert(NW <= 8 && TB / kChunk <= 256 && UB % kChunk == 0 && kChunk % JU == 0 &&
                       NW * UPS <= 32,
                   "job fields");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned col = hist + 4u * (unsigned)tid;
+    const unsigned col = hist + 4u * (unsigned)(HM == kHistWarpRed ? warp : tid);
     const bool stats = ST && p.stats != nullptr;
     unsigned fills = 0;      // jobs waiting per kind, 8 bits each
     unsigned diag_units = 0;  // diagonal units taken (bit sub UPS + u)
@@ -1397,13 +1406,13 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
             const float4 gb = make_float4(__uint_as_float(gbu.x), __uint_as_float(gbu.y),
                                           __uint_as_float(gbu.z), __uint_as_float(gbu.w));
             unsigned rlo = 0;
-            const unsigned trash = (unsigned)(p.tab.K + 1) << row_shift;
+            const unsigned trash = (unsigned)(p.tab.K + 1) * row_bytes;
             const int mode = span_class(ga, gb, lut, p.tab.shift, p.tab.base, p.tab.n_lut - 1,
-                                        row_shift, rlo, p.tab.h_top, trash);
+                                        row_bytes, rlo, p.tab.h_top, trash);
             if (mode == 0) {
                 if (rlo != trash) hist_add<HM>(col + rlo, NP);  // the trash row is never read
             } else {
-                kj = job_word(lane, (warp + k) % NW, c, rlo >> row_shift) |
+                kj = job_word(lane, (warp + k) % NW, c, rlo / row_bytes) |
                      ((unsigned)(mode == 1 ? kJobTwo + 1 : mode == 3 ? kJobThree + 1
                                                                      : kJobExact + 1) << 30);
             }
@@ -1537,7 +1546,7 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
 template <int NT, int R, int JU, int HM, int DEF, bool ST>
 __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __grid_constant__ PairParams p) {
     using PK = PairKernel<NT, R, JU, HM, DEF>;
-    constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS;
+    constexpr int TA = PK::TA, TB = PK::TB, HCOLS = PK::HCOLS, HSTRIDE = PK::HSTRIDE;
     constexpr int NW = NT / 32, SA = 32 * R, UPS = 4, UB = TB / UPS;
     static_assert(TA == NW * SA && TB % UPS == 0, "units tile the item");
     __shared__ unsigned s_units[NW];
@@ -1559,7 +1568,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
     __shared__ unsigned long long s_stat[3];  // span-path rechecks, span pairs, skipped pairs
 
     const int tid = threadIdx.x;
-    const unsigned row_bytes = HCOLS * 4u;
+    constexpr unsigned row_bytes = PK::ROWB;
     for (int q = tid; q < p.tab.n_lut; q += NT)
         sLut[q] = make_uint4(p.tab.lut[q][0], p.tab.lut[q][1], p.tab.lut[q][2] * row_bytes,
                              p.tab.lut[q][3] * row_bytes);
@@ -1567,7 +1576,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
         sC[q] = p.tab.c64[q];
         sBand[q] = make_uint2(p.tab.band[q][0], p.tab.band[q][1]);
     }
-    for (int q = tid; q < (K + 2) * HCOLS; q += NT) hist[q] = 0u;
+    for (int q = tid; q < (K + 2) * HSTRIDE; q += NT) hist[q] = 0u;
     if (tid < 3) s_stat[tid] = 0ull;
 
     // the current count lives in shared memory; thread 0 switches it when an
@@ -1612,7 +1621,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
         const int seg = s_seg;
         if (seg != cur_seg) {
             if (cur_seg != -2 && since_flush > 0) {
-                flush_hist<NT, HCOLS>(hist, K, sSeg.counts);
+                flush_hist<NT, HCOLS, HSTRIDE>(hist, K, sSeg.counts);
                 since_flush = 0;
             }
             __syncthreads();  // flush done before the segment is replaced
@@ -1683,13 +1692,13 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
         ++n_items;
         if (++since_flush == p.items_per_flush) {
             __syncthreads();
-            flush_hist<NT, HCOLS>(hist, K, sSeg.counts);
+            flush_hist<NT, HCOLS, HSTRIDE>(hist, K, sSeg.counts);
             __syncthreads();
             since_flush = 0;
         }
     }
     // all threads left the loop after the same barrier
-    if (cur_seg != -2) flush_hist<NT, HCOLS>(hist, K, sSeg.counts);
+    if (cur_seg != -2) flush_hist<NT, HCOLS, HSTRIDE>(hist, K, sSeg.counts);
     if (p.stats) {
         unsigned long long v = n_recheck;
 #pragma unroll
@@ -1744,7 +1753,8 @@ const Variant* variants(int* n) {
         make_variant<128, 8, 1, kHistLaneAtomic, 1>(), make_variant<64, 16, 2, kHistLaneAtomic, 1>(),
         make_variant<64, 16, 2, kHistWarp, 0>(),       make_variant<128, 16, 2, kHistLaneAtomic, 1>(),
         make_variant<256, 8, 2, kHistLaneAtomic, 1>(), make_variant<256, 8, 2, kHistWarp, 0>(),
-        make_variant<64, 8, 2, kHistLaneAtomic, 0>(),
+        make_variant<64, 8, 2, kHistLaneAtomic, 0>(),  make_variant<128, 8, 2, kHistWarpRed, 0>(),
+        make_variant<64, 8, 2, kHistWarpRed, 0>(),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;
@@ -1801,8 +1811,14 @@ const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, int max_s
         return x.nt == want_nt && x.r == want_r && x.ju == want_ju;
     };
     if (want_hm == 0) {
-        // private per-thread histograms while they fit comfortably
+        // private per-thread histograms while they fit comfortably (measured
+        // 15% faster on the survey workload than per-warp columns, whose shared
+        // reductions contend); per-warp columns updated by shared reductions
+        // otherwise, which keep the span path at large bin counts
         want_hm = kHistWarp;
+        for (int i = 0; i < nv; ++i)
+            if (shape(v[i]) && v[i].hm == kHistWarpRed && v[i].def == 0 && fits(v[i]))
+                want_hm = kHistWarpRed;
         for (int i = 0; i < nv; ++i)
             if (shape(v[i]) && v[i].hm == kHistLaneAtomic && v[i].smem(K, n_lut) <= 100 * 1024)
                 want_hm = kHistLaneAtomic;
@@ -1810,10 +1826,12 @@ const Variant* pick_variant(const wtheta_tune* tune, int K, int n_lut, int max_s
     if (want_def < 0) want_def = 0;  // inline binning measured faster once in-range pairs matter
     for (int i = 0; i < nv; ++i)
         if (shape(v[i]) && v[i].hm == want_hm && v[i].def == want_def && fits(v[i])) return &v[i];
-    // fall back: same tile size, per-warp histograms
-    for (int i = 0; i < nv; ++i)
-        if (v[i].nt * v[i].r == want_nt * want_r && v[i].hm == kHistWarp && fits(v[i]))
-            return &v[i];
+    // fall back: same tile size, per-warp histograms (with span jobs first)
+    for (int hm : {(int)kHistWarpRed, (int)kHistWarp})
+        for (int i = 0; i < nv; ++i)
+            if (v[i].nt * v[i].r == want_nt * want_r && v[i].hm == hm && v[i].def == 0 &&
+                fits(v[i]))
+                return &v[i];
     return nullptr;
 }
 
@@ -2005,7 +2023,8 @@ unsigned long long per_item_bound(const Variant* v) {
     // as much.
     const unsigned long long own = (unsigned long long)(v->nt / 32) * (unsigned long long)v->r *
                                    (unsigned long long)v->nt * (unsigned long long)v->r;
-    return (v->hm == kHistWarp ? 32ull : 1ull) * (2ull * own + 3ull * 32ull * (unsigned)v->r);
+    return (v->hm == kHistWarp || v->hm == kHistWarpRed ? 32ull : 1ull) *
+           (2ull * own + 3ull * 32ull * (unsigned)v->r);
 }
 
 Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
@@ -2065,7 +2084,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
         return WTHETA_EINVAL;
     }
     if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
-                 tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
+                 tune->hist_mode > 4 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
                  tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0 ||
                  tune->skip_far < 0 || tune->skip_far > 2 || tune->span_bins < 0 ||
                  tune->span_bins > 2))
@@ -2170,6 +2189,8 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
 
 // Pairs (i < j) of an auto count of n points whose first point i is in the
 // sorted rows [r0, r1).
+// Pairs (i < j) of an auto count of n points whose first point i is in the
+// sorted rows [r0, r1).
 static unsigned long long auto_pairs_in_rows(long long n, long long r0, long long r1) {
     if (r1 <= r0) return 0ull;
     const unsigned long long a = (unsigned long long)r0, b = (unsigned long long)r1;
@@ -2203,7 +2224,7 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
         (is_xyz != 0 && is_xyz != 1) || n_shards < 1 || shard < 0 || shard >= n_shards)
         return WTHETA_EINVAL;
     if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
-                 tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
+                 tune->hist_mode > 4 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
                  tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0 ||
                  tune->skip_far < 0 || tune->skip_far > 2 || tune->span_bins < 0 ||
                  tune->span_bins > 2))
@@ -2877,7 +2898,7 @@ static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, int is_x
         if (c.n_data < 2 || c.n_rand < 2 || !c.data || !c.rand) return WTHETA_EINVAL;
     }
     if (tune && (tune->threads < 0 || tune->points_per_thread < 0 || tune->hist_mode < 0 ||
-                 tune->hist_mode > 3 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
+                 tune->hist_mode > 4 || tune->j_per_screen < 0 || tune->j_per_screen > 2 ||
                  tune->deferred < 0 || tune->deferred > 2 || tune->blocks_per_sm < 0 ||
                  tune->skip_far < 0 || tune->skip_far > 2 || tune->span_bins < 0 ||
                  tune->span_bins > 2))

@@ -115,7 +115,10 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
     // K >= 1 and the edges increase, so c_K > 0 and there is at least one band.
     t->h_top = bands[n_bands - 1].hi;
     const uint32_t lo_first = bands[0].lo;
-    int best_shift = -1, best_complex = 1 << 30;
+    // the shift whose buckets holding several bands cover the least of the
+    // range (their values go through a band search), the coarsest on ties
+    int best_shift = -1;
+    long long best_width = -1;
     for (int shift = 30; shift >= 0; --shift) {
         long long n = (long long)(t->h_top >> shift) - (long long)(lo_first >> shift) + 1;
         if (n > kMaxLut) break;
@@ -135,8 +138,9 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
                 }
             }
         }
-        if (complex_buckets < best_complex) {
-            best_complex = complex_buckets;
+        const long long width = (long long)complex_buckets << shift;
+        if (best_width < 0 || width < best_width) {
+            best_width = width;
             best_shift = shift;
         }
         if (complex_buckets == 0) break;
@@ -171,8 +175,9 @@ int build_table(const double* edges_deg, int K, BinTable* t) {
             e[0] = bands[which].lo; e[1] = bands[which].hi;
             e[2] = (uint32_t)bands[which].k; e[3] = (uint32_t)(bands[which].k + 1);
         } else {
-            // every in-range value of the bucket is rechecked in FP64; one
-            // beyond the top edge (only the top bucket can hold one) is overflow
+            // every in-range value of the bucket is placed by a search of the
+            // bands (FP64 only inside one); one beyond the top edge (only the
+            // top bucket can hold one) is overflow
             e[0] = 0u; e[1] = t->h_top;
             e[2] = (uint32_t)(K + 1); e[3] = (uint32_t)(K + 1);
             ++t->n_complex;

@@ -40,7 +40,13 @@ struct BinTable {
 };
 
 
-enum HistMode { kHistLane = 1, kHistWarp = 2, kHistLaneAtomic = 3 };
+// Private histogram columns of the pair kernel: per thread, plain
+// read-modify-write (1); per warp, lanes merged by __match_any_sync (2); per
+// thread, shared reduction (3); per warp, shared reduction (4: the shared
+// atomic unit merges lanes that hit one word at full rate, and the rows of a
+// warp's column sit an odd number of words apart so that different rows hit
+// different banks).
+enum HistMode { kHistLane = 1, kHistWarp = 2, kHistLaneAtomic = 3, kHistWarpRed = 4 };
 
 // One count: catalogue a against catalogue b (auto: a = b, pairs i < j).
 struct Segment {

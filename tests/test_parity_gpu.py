@@ -23,7 +23,8 @@ ARCMIN = 1.0 / 60.0
 # screening test, histogram mode, deferred binning)
 SHAPES = [(128, 8, 2, 3, 2), (128, 8, 2, 3, 1), (128, 8, 2, 1, 2), (128, 8, 2, 2, 1),
           (128, 8, 1, 3, 2), (64, 16, 2, 3, 2), (64, 16, 2, 2, 1), (128, 16, 2, 3, 2),
-          (256, 8, 2, 3, 2), (256, 8, 2, 2, 1), (64, 8, 2, 3, 1)]
+          (256, 8, 2, 3, 2), (256, 8, 2, 2, 1), (64, 8, 2, 3, 1), (128, 8, 2, 4, 1),
+          (64, 8, 2, 4, 1)]
 VARIANTS = [dict(threads=a, points_per_thread=b, j_per_screen=c, hist_mode=d, deferred=f)
             for a, b, c, d, f in SHAPES]
 
@@ -298,7 +299,7 @@ def test_shards_sum_to_the_whole_count(W, is_auto):
 
 def test_wtheta_shards_sum_to_the_oracle_and_balance_work(W):
     """wtheta_count_wtheta_shard: every shard's 3 (K+2) counts are exact for
-    the pairs of its tile rows (their slots sum to its pairs), the shards add
+    the pairs of its tile columns (their slots sum to its pairs), the shards add
     up, slot by slot, to the oracle's whole DD, DR and RR (P1: the oracle's
     unit vectors), and shards of a clustered survey get similar numbers of
     kept tile pairs (the split's weights) -- Sec. 5's division of the data set
