@@ -250,8 +250,13 @@ __device__ __forceinline__ unsigned cell_key(double x, double y, double z, int L
 // per-chunk settling of pairs both rely on.
 constexpr int kSortLevel = 14;
 constexpr int kSortThreads = 256;
-constexpr int kSortRounds = 16;
-constexpr long long kSortTile = (long long)kSortThreads * kSortRounds;  // keys per block
+// Rounds of 256 keys per block of the sort: enough blocks for about two per
+// SM of a large GPU (at most 16 rounds), so that a small catalogue's passes
+// are short, one round each, instead of a few blocks looping over 16 rounds.
+static inline int sort_rounds(long long n) {
+    const long long r = (n + 256LL * 304 - 1) / (256LL * 304);
+    return (int)std::min<long long>(std::max<long long>(r, 1), 16);
+}
 
 __global__ void k_sort_keys(const double* __restrict__ xyz, long long stride, long long n,
                             int check, unsigned* __restrict__ key, unsigned* __restrict__ idx) {
@@ -266,13 +271,14 @@ __global__ void k_sort_keys(const double* __restrict__ xyz, long long stride, lo
 
 // hist[d * n_blocks + b] = keys of block b whose digit is d.
 __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const unsigned* __restrict__ key,
-                                                             long long n, int shift,
+                                                             long long n, int shift, int rounds,
                                                              unsigned* __restrict__ hist) {
     __shared__ unsigned cnt[256];
     const int t = threadIdx.x;
     cnt[t] = 0;
     __syncthreads();
-    const long long lo = blockIdx.x * kSortTile, hi = min(lo + kSortTile, n);
+    const long long tile = (long long)kSortThreads * rounds;
+    const long long lo = blockIdx.x * tile, hi = min(lo + tile, n);
     for (long long i = lo + t; i < hi; i += kSortThreads) atomicAdd(&cnt[(key[i] >> shift) & 255u], 1u);
     __syncthreads();
     hist[(long long)t * gridDim.x + blockIdx.x] = cnt[t];
@@ -283,14 +289,14 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const unsigned* __r
 // round, warps in order and lanes in order).
 __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
     const unsigned* __restrict__ key_in, const unsigned* __restrict__ idx_in, long long n,
-    int shift, const unsigned* __restrict__ offs, unsigned* __restrict__ key_out,
+    int shift, int rounds, const unsigned* __restrict__ offs, unsigned* __restrict__ key_out,
     unsigned* __restrict__ idx_out) {
     __shared__ unsigned base[256];
     __shared__ unsigned wcnt[kSortThreads / 32][256];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     base[t] = offs[(long long)t * gridDim.x + blockIdx.x];
-    const long long lo = blockIdx.x * kSortTile;
-    for (int r = 0; r < kSortRounds; ++r) {
+    const long long lo = blockIdx.x * (long long)kSortThreads * rounds;
+    for (int r = 0; r < rounds; ++r) {
 #pragma unroll
         for (int q = 0; q < kSortThreads / 32; ++q) wcnt[q][t] = 0;
         __syncthreads();
@@ -322,14 +328,24 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
     }
 }
 
-// Exclusive prefix sum in place (one block of 1024).
+// Exclusive prefix sum in place (one block of 1024).  Up to kScanStage
+// values are first staged in shared memory by coalesced loads (each thread
+// then scans a contiguous run of them there); longer arrays are read in place.
+constexpr int kScanStage = 8192;
 __global__ void __launch_bounds__(1024) k_exclusive_scan(unsigned* __restrict__ a, int n) {
     __shared__ unsigned warp_sum[32];
+    __shared__ unsigned stage[kScanStage];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const bool staged = n <= kScanStage;
+    if (staged) {
+        for (int i = t; i < n; i += 1024) stage[i] = a[i];
+        __syncthreads();
+    }
+    unsigned* v = staged ? stage : a;
     const int per = (n + 1023) / 1024;
     const int lo = min(t * per, n), hi = min(lo + per, n);
     unsigned sum = 0;
-    for (int i = lo; i < hi; ++i) sum += a[i];
+    for (int i = lo; i < hi; ++i) sum += v[i];
     unsigned incl = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -350,9 +366,13 @@ __global__ void __launch_bounds__(1024) k_exclusive_scan(unsigned* __restrict__ 
     __syncthreads();
     unsigned run = incl - sum + (w > 0 ? warp_sum[w - 1] : 0u);
     for (int i = lo; i < hi; ++i) {
-        const unsigned c = a[i];
-        a[i] = run;
+        const unsigned c = v[i];
+        v[i] = run;
         run += c;
+    }
+    if (staged) {
+        __syncthreads();
+        for (int i = t; i < n; i += 1024) a[i] = stage[i];
     }
 }
 
@@ -1754,7 +1774,7 @@ const Variant* variants(int* n) {
         make_variant<64, 16, 2, kHistWarp, 0>(),       make_variant<128, 16, 2, kHistLaneAtomic, 1>(),
         make_variant<256, 8, 2, kHistLaneAtomic, 1>(), make_variant<256, 8, 2, kHistWarp, 0>(),
         make_variant<64, 8, 2, kHistLaneAtomic, 0>(),  make_variant<128, 8, 2, kHistWarpRed, 0>(),
-        make_variant<64, 8, 2, kHistWarpRed, 0>(),
+        make_variant<64, 8, 2, kHistWarpRed, 0>(),     make_variant<32, 8, 2, kHistLaneAtomic, 0>(),
     };
     *n = (int)(sizeof(v) / sizeof(v[0]));
     return v;
@@ -1783,14 +1803,15 @@ int device_info(DeviceInfo* out) {
     return WTHETA_OK;
 }
 
-// The default shape for one call: tiles of 512 points (64 threads) when the
-// larger catalogue has at most 64k points, so that a small count still has
-// tile pairs for every SM; the 1024-point shape otherwise.
+// The default shape for one call: tiles of 256 points (one warp) when the
+// larger catalogue has at most 16k points and of 512 points (64 threads) up
+// to 64k, so that a small count still has tile pairs for every SM and each
+// CTA's share stays short; the 1024-point shape otherwise.
 const Variant* pick_for_size(const wtheta_tune* tune, long long n_max, int K, int n_lut,
                              int max_smem) {
     if (!tune && n_max <= 65536) {
         wtheta_tune small = {};
-        small.threads = 64;
+        small.threads = n_max <= 16384 ? 32 : 64;
         small.points_per_thread = 8;
         const Variant* v = pick_variant(&small, K, n_lut, max_smem);
         if (v) return v;
@@ -1877,7 +1898,8 @@ static int launch_grid(long long n, int sm_count) {
 }
 
 static long long sort_blocks(long long n) {
-    return std::max<long long>(1, (n + kSortTile - 1) / kSortTile);
+    const long long tile = (long long)kSortThreads * sort_rounds(n);
+    return std::max<long long>(1, (n + tile - 1) / tile);
 }
 
 size_t order_bytes(long long n, int with_labels) {
@@ -1891,6 +1913,7 @@ int spatial_order(const double* x64, long long stride, long long n, int check,
                   cudaStream_t st, const unsigned** order, const unsigned** sorted_labels) {
     const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
     const long long G = sort_blocks(n);
+    const int rounds = sort_rounds(n);
     unsigned* key[2] = {(unsigned*)scratch, (unsigned*)(scratch + a4)};
     unsigned* idx[2] = {(unsigned*)(scratch + 2 * a4), (unsigned*)(scratch + 3 * a4)};
     unsigned* lab = (unsigned*)(scratch + 4 * a4);
@@ -1902,9 +1925,10 @@ int spatial_order(const double* x64, long long stride, long long n, int check,
     count_launch();
     for (int pass = 0; pass < 4; ++pass) {
         const int in = pass & 1, o = in ^ 1;
-        k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], n, 8 * pass, hist);
+        k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], n, 8 * pass, rounds, hist);
         k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
-        k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], idx[in], n, 8 * pass, hist,
+        k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], idx[in], n, 8 * pass, rounds,
+                                                              hist,
                                                               key[o], idx[o]);
         count_launch(3);
     }
@@ -1913,9 +1937,9 @@ int spatial_order(const double* x64, long long stride, long long n, int check,
         // one more stable pass, on the label: regions in label order, each in
         // spatial order
         k_sorted_labels<<<launch_grid(n, sm_count), 256, 0, st>>>(idx[0], labels, n, n_labels, lab);
-        k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(lab, n, 0, hist);
+        k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(lab, n, 0, rounds, hist);
         k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
-        k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(lab, idx[0], n, 0, hist, key[1],
+        k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(lab, idx[0], n, 0, rounds, hist, key[1],
                                                               idx[1]);
         count_launch(4);
         *order = idx[1];

@@ -13,7 +13,9 @@
 //     every admitted, ready request: small requests first (up to half of a
 //     round), then the others in arrival order; a request that arrives while
 //     others are counting joins the next round instead of queueing behind them
-//     (rounds double while the backlog is deep);
+//     (rounds double while the backlog is deep); two rounds are in flight on
+//     two streams, so that the next round's CTAs fill the SMs that the
+//     current round's last CTAs leave idle;
 //   - completion: after the round that holds a request's last tile pairs, the
 //     overflow slots and the copy of its counts to the host are queued on the
 //     same stream, so its counts are final when its event fires; w(theta) is
@@ -68,6 +70,8 @@ struct Request {
 };
 
 struct Round {
+    cudaStream_t st = nullptr;     // its own stream: the next round's CTAs start as this
+                                   // round's retire, so launch tails overlap
     Segment* d_segs = nullptr;
     Segment* h_segs = nullptr;     // pinned staging of the table
     int cap = 0;
@@ -93,7 +97,7 @@ struct wtheta_server {
     size_t resident = 0;
     long long round_items = 0;
     int max_active = 0;
-    cudaStream_t up = nullptr, comp = nullptr;
+    cudaStream_t up = nullptr;
     Round rounds[2];
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -262,8 +266,8 @@ long long remaining(const Request* r) {
     return x;
 }
 
-// Builds and launches one round on the compute stream; returns true if it
-// launched one.  Called with the server lock held.
+// Builds and launches one round on its stream; returns true if it launched
+// one.  Called with the server lock held.
 bool launch_round(wtheta_server* S, Round& R) {
     TraceRange trace("server_round");
     std::vector<Request*> ready;
@@ -324,36 +328,40 @@ bool launch_round(wtheta_server* S, Round& R) {
         if (remaining(r) == 0) finishing.push_back(r);
     }
     if (n == 0 && finishing.empty()) return false;
-    // every request in the round must be ready on the compute stream
-    for (Request* r : ready) cudaStreamWaitEvent(S->comp, r->ready, 0);
+    // every request in the round must be ready on the round's stream
+    for (Request* r : ready) cudaStreamWaitEvent(R.st, r->ready, 0);
     int rc = WTHETA_OK;
     if (n > 0) {
         rc = check_cuda(cudaMemcpyAsync(R.d_segs, R.h_segs, sizeof(Segment) * n,
-                                        cudaMemcpyHostToDevice, S->comp));
-        if (!rc) rc = check_cuda(cudaMemsetAsync(R.d_cursor, 0, 8, S->comp));
+                                        cudaMemcpyHostToDevice, R.st));
+        if (!rc) rc = check_cuda(cudaMemsetAsync(R.d_cursor, 0, 8, R.st));
         const int grid = (int)std::min<long long>(S->grid, items);
         PairParams prm = make_params(S->v, S->tab, nullptr, R.d_segs, n, 0, items, R.d_cursor,
                                      nullptr);
         prm.span = S->span;
-        if (!rc) rc = launch_pairs(S->v, prm, grid, S->smem, S->comp);
+        if (!rc) rc = launch_pairs(S->v, prm, grid, S->smem, R.st);
         ++S->kernels;
     }
     // requests whose last tile pairs are in this round: overflow slots, then
-    // their counts to the host, in stream order after the round
+    // their counts to the host, in stream order after the round and after the
+    // other round in flight (which may hold earlier tile pairs of theirs)
+    if (!finishing.empty())
+        for (Round& O : S->rounds)
+            if (&O != &R && O.busy) cudaStreamWaitEvent(R.st, O.done, 0);
     for (Request* r : finishing) {
-        if (!rc) rc = launch_finalize_segments(r->d_segs, r->ncount, S->K, S->comp);
+        if (!rc) rc = launch_finalize_segments(r->d_segs, r->ncount, S->K, R.st);
         ++S->kernels;
         if (!rc)
             rc = check_cuda(cudaMemcpyAsync(r->host_counts, r->d_counts,
                                             (size_t)r->ncount * (S->K + 2) * 8,
-                                            cudaMemcpyDeviceToHost, S->comp));
-        if (!rc) rc = check_cuda(cudaFreeAsync(r->dmem, S->comp));
+                                            cudaMemcpyDeviceToHost, R.st));
+        if (!rc) rc = check_cuda(cudaFreeAsync(r->dmem, R.st));
         if (!rc) r->dmem = nullptr;
-        if (!rc) rc = check_cuda(cudaEventRecord(r->finished, S->comp));
+        if (!rc) rc = check_cuda(cudaEventRecord(r->finished, R.st));
         r->state = rc ? kFailed : kFinishing;
         r->status = rc;
     }
-    if (!rc) rc = check_cuda(cudaEventRecord(R.done, S->comp));
+    if (!rc) rc = check_cuda(cudaEventRecord(R.done, R.st));
     R.busy = !rc;
     ++S->n_rounds;
     S->items_done += items;
@@ -457,12 +465,19 @@ int server_create(const double* edges, int K, size_t budget, int max_active,
         // each launch stays small
         S->round_items = 48LL * S->grid;
     }
-    if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&S->up, cudaStreamNonBlocking));
-    if (!rc) rc = check_cuda(cudaStreamCreateWithFlags(&S->comp, cudaStreamNonBlocking));
+    // the upload stream runs at the highest priority: its short preparation
+    // kernels take the SM slots that a round's last CTAs free before the CTAs
+    // of the round waiting behind it, so a new request does not wait for whole
+    // rounds to become ready
+    int prio_low = 0, prio_high = 0;
+    if (!rc) rc = check_cuda(cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high));
+    if (!rc)
+        rc = check_cuda(cudaStreamCreateWithPriority(&S->up, cudaStreamNonBlocking, prio_high));
     for (Round& R : S->rounds) {
         if (rc) break;
         R.cap = 4096;
-        rc = dev_malloc((void**)&R.d_segs, sizeof(Segment) * R.cap);
+        rc = check_cuda(cudaStreamCreateWithFlags(&R.st, cudaStreamNonBlocking));
+        if (!rc) rc = dev_malloc((void**)&R.d_segs, sizeof(Segment) * R.cap);
         if (!rc) rc = check_cuda(cudaMallocHost(&R.h_segs, sizeof(Segment) * R.cap));
         if (!rc) rc = dev_malloc((void**)&R.d_cursor, 8);
         if (!rc) rc = check_cuda(cudaEventCreateWithFlags(&R.done, cudaEventDisableTiming));
@@ -624,7 +639,8 @@ int wtheta_server_destroy(wtheta_server* S) {
     S->cv_work.notify_all();
     if (S->worker.joinable()) S->worker.join();
     cudaSetDevice(S->dev);
-    if (S->comp) cudaStreamSynchronize(S->comp);
+    for (Round& R : S->rounds)
+        if (R.st) cudaStreamSynchronize(R.st);
     if (S->up) cudaStreamSynchronize(S->up);
     for (auto& kv : S->all) {
         Request* r = kv.second;
@@ -637,9 +653,9 @@ int wtheta_server_destroy(wtheta_server* S) {
         if (R.h_segs) cudaFreeHost(R.h_segs);
         if (R.d_cursor) cudaFree(R.d_cursor);
         if (R.done) cudaEventDestroy(R.done);
+        if (R.st) cudaStreamDestroy(R.st);
     }
     if (S->up) cudaStreamDestroy(S->up);
-    if (S->comp) cudaStreamDestroy(S->comp);
     delete S;
     return WTHETA_OK;
 }

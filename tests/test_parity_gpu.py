@@ -24,7 +24,7 @@ ARCMIN = 1.0 / 60.0
 SHAPES = [(128, 8, 2, 3, 2), (128, 8, 2, 3, 1), (128, 8, 2, 1, 2), (128, 8, 2, 2, 1),
           (128, 8, 1, 3, 2), (64, 16, 2, 3, 2), (64, 16, 2, 2, 1), (128, 16, 2, 3, 2),
           (256, 8, 2, 3, 2), (256, 8, 2, 2, 1), (64, 8, 2, 3, 1), (128, 8, 2, 4, 1),
-          (64, 8, 2, 4, 1)]
+          (64, 8, 2, 4, 1), (32, 8, 2, 3, 1)]
 VARIANTS = [dict(threads=a, points_per_thread=b, j_per_screen=c, hist_mode=d, deferred=f)
             for a, b, c, d, f in SHAPES]
 
