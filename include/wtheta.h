@@ -266,8 +266,12 @@ int wtheta_count_wtheta_shard(const double* coords_d, int64_t n_d, const double*
  *     batches of similar size and bin count); else the given shape.
  *   stream: used for the plan-time preparation and autotuning.
  *   *plan: receives the plan; free it with wtheta_batch_free.
- * The plan owns its scratch (FP32/FP64 copies of every catalogue), its work
- * table and its graph.
+ * 1 <= n_cats <= 32768.  The plan owns its scratch (FP32/FP64 copies of every
+ * catalogue), its work table and its graph.  The catalogues are prepared
+ * together on every run, by a constant number of launches whatever n_cats:
+ * one conversion into a single FP64 array, one spatial sort by (catalogue,
+ * key), one gather into FP32 copies with each catalogue on tile boundaries,
+ * one pass of chunk spheres and one of tile caps.
  */
 typedef struct wtheta_catalog_pair {
     const double* data;
@@ -294,8 +298,8 @@ int wtheta_batch_plan_ex(const wtheta_catalog_pair* cats, int32_t n_cats, int32_
                          void* stream, wtheta_plan** plan);
 
 /*
- * Runs a plan: one graph replay (conversion and spatial ordering of every
- * catalogue, the single pair-count launch, the overflow slots), then copies
+ * Runs a plan: one graph replay (the shared preparation of every catalogue,
+ * the single pair-count launch, the overflow slots), then copies
  * the counts to counts: device, n_cats x 3 x (K+2) uint64, laid out
  * [cat][DD, DR, RR][slot].  Asynchronous on stream.
  */

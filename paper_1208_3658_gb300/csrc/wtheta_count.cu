@@ -435,7 +435,11 @@ __global__ void k_count_labels(const unsigned* __restrict__ lab, long long n, in
 
 // FP32 copies with every region starting on a tile boundary: region r's
 // points (sorted positions src[r] .. src[r+1]-1) go to dst[r] .., the rest of
-// its last tile holds sentinels.  dst[R] = n_pad.
+// its last tile holds sentinels.  dst[R] = n_pad.  A sentinel is numbered
+// within its region (below the tile size) and tagged by its region and
+// array, so that no two sentinels a count can pair coincide in FP32 (numbered
+// by their position in a long array, sentinels more than 2^24 points in would
+// round onto one another).
 __global__ void k_gather_regions(const double* __restrict__ xyz, long long stride,
                                  const unsigned* __restrict__ order,
                                  const long long* __restrict__ src,
@@ -448,13 +452,47 @@ __global__ void k_gather_regions(const double* __restrict__ xyz, long long strid
             const int mid = (lo + hi + 1) >> 1;
             if (dst[mid] <= i) lo = mid; else hi = mid - 1;
         }
-        const long long j = i - dst[lo];
-        if (j < src[lo + 1] - src[lo]) {
+        const long long j = i - dst[lo], n_lo = src[lo + 1] - src[lo];
+        if (j < n_lo) {
             const long long k = order[src[lo] + j];
             p32[i] = point32(xyz[k], xyz[stride + k], xyz[2 * stride + k], k);
         } else {
-            p32[i] = sentinel32(tag, i);
+            p32[i] = sentinel32(2 * lo + tag, j - n_lo);
         }
+    }
+}
+
+// The catalogues of a batch into one FP64 SoA array (stride N) with a label
+// per point (its catalogue): catalogue c's points go to positions
+// [off[c], off[c + 1]), converted from RA/Dec or copied from unit vectors.
+struct BatchCat {
+    const double* src;   // interleaved RA/Dec degrees, or SoA unit vectors (3 n)
+    long long n;
+};
+__global__ void k_batch_gather(const BatchCat* __restrict__ cats, const long long* __restrict__ off,
+                               int n_cats, int is_xyz, long long N, double* __restrict__ x,
+                               int* __restrict__ lab) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_cats - 1;  // last catalogue with off <= i
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= i) lo = mid; else hi = mid - 1;
+        }
+        const BatchCat c = cats[lo];
+        const long long j = i - off[lo];
+        double px, py, pz;
+        if (is_xyz) {
+            px = c.src[j];
+            py = c.src[c.n + j];
+            pz = c.src[2 * c.n + j];
+        } else {
+            radec_unit(c.src[2 * j], c.src[2 * j + 1], px, py, pz);
+        }
+        x[i] = px;
+        x[N + i] = py;
+        x[2 * N + i] = pz;
+        lab[i] = lo;
     }
 }
 
@@ -1934,16 +1972,22 @@ int spatial_order(const double* x64, long long stride, long long n, int check,
     }
     // four passes: the order is back in the first buffers
     if (labels) {
-        // one more stable pass, on the label: regions in label order, each in
-        // spatial order
-        k_sorted_labels<<<launch_grid(n, sm_count), 256, 0, st>>>(idx[0], labels, n, n_labels, lab);
-        k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(lab, n, 0, rounds, hist);
-        k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
-        k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(lab, idx[0], n, 0, rounds, hist, key[1],
-                                                              idx[1]);
-        count_launch(4);
-        *order = idx[1];
-        if (sorted_labels) *sorted_labels = key[1];
+        // one more stable pass per byte of the label (two above 256 labels):
+        // regions in label order, each in spatial order
+        int cur = 0;
+        for (int shift = 0; shift == 0 || (shift < 16 && (n_labels - 1) >> shift); shift += 8) {
+            k_sorted_labels<<<launch_grid(n, sm_count), 256, 0, st>>>(idx[cur], labels, n, n_labels,
+                                                                      lab);
+            k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(lab, n, shift, rounds, hist);
+            k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
+            k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(lab, idx[cur], n, shift, rounds,
+                                                                  hist, key[cur ^ 1],
+                                                                  idx[cur ^ 1]);
+            count_launch(4);
+            cur ^= 1;
+        }
+        *order = idx[cur];
+        if (sorted_labels) *sorted_labels = key[cur];
     }
     return check_cuda(cudaGetLastError());
 }
@@ -2615,6 +2659,19 @@ struct wtheta_plan {
     void* scratch = nullptr;               // prepared copies of every catalogue
     std::vector<wtheta::Prepared> prep;    // 2 per catalogue pair
     std::vector<long long> n_pad;
+    // all catalogues (data 2m, randoms 2m + 1) are prepared together: one FP64
+    // array of every point, one sort by (catalogue, spatial key), FP32 copies
+    // with every catalogue starting on a tile boundary
+    std::vector<long long> src_off, dst_off;  // 2 n_cats + 1 each
+    long long n_all = 0, n_all_pad = 0;
+    wtheta::BatchCat* d_cats = nullptr;
+    long long* d_src_off = nullptr;         // src_off, then dst_off (for the gather)
+    double* x_all = nullptr;
+    int* lab_all = nullptr;
+    unsigned char* sort_scratch = nullptr;
+    float4* p32_all = nullptr;
+    float4* c32_all = nullptr;
+    wtheta::TileCap* caps_all = nullptr;
     wtheta::Segment* d_segs = nullptr;
     int n_segs = 0;
     long long total_items = 0;
@@ -2636,6 +2693,7 @@ struct wtheta_plan {
     unsigned long long* d_total = nullptr;    // kept items of the run
     unsigned long long* d_stats = nullptr;    // WTHETA_NSTATS of the last run
     std::vector<wtheta::TileCap*> caps;       // per catalogue
+    int sm_count = 0;
 };
 
 namespace wtheta {
@@ -2661,38 +2719,100 @@ static void store_tuned(const TuneKey& k, int idx) {
     g_tune_cache.push_back({k, idx});
 }
 
+// Preparation of every catalogue of a plan, as one pipeline over all of them
+// (a constant number of launches whatever the number of catalogues):
+// conversion into one FP64 array with a catalogue label per point, one
+// spatial sort by (catalogue, key), FP32 copies with every catalogue starting
+// on a tile boundary (sentinels in the rest of its last tile), chunk spheres
+// and, when far tile pairs are skipped, tile caps.  Reads the catalogues'
+// current contents (the graph replays it on every run).
+static int batch_prepare(wtheta_plan* P, int T, cudaStream_t st) {
+    const int nc2 = 2 * P->n_cats;
+    if (P->n_all <= 0) return WTHETA_OK;
+    k_batch_gather<<<launch_grid(P->n_all, P->sm_count), 256, 0, st>>>(
+        P->d_cats, P->d_src_off, nc2, P->is_xyz, P->n_all, P->x_all, P->lab_all);
+    count_launch();
+    const unsigned* order = nullptr;
+    int rc = spatial_order(P->x_all, P->n_all, P->n_all, P->is_xyz, P->lab_all, nc2,
+                           P->sort_scratch, P->sm_count, st, &order, nullptr);
+    if (!rc)
+        rc = launch_gather_regions(P->x_all, P->n_all, order, P->d_src_off, P->d_src_off + nc2 + 1,
+                                   nc2, P->n_all_pad, P->p32_all, 0, P->sm_count, st);
+    if (!rc) rc = launch_chunk_caps(P->p32_all, P->n_all_pad, P->c32_all, P->sm_count, st);
+    if (!rc && P->cull)
+        rc = launch_tile_caps(P->p32_all, P->n_all_pad, T, P->n_all_pad / T, P->caps_all, st);
+    return rc;
+}
+
 // Lays out the plan's scratch and work table for one kernel shape (its tile
 // T = threads x points_per_thread), prepares every catalogue on stream st.
 static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStream_t st) {
     const long long T = (long long)v->nt * v->r;
-    const int nc = P->n_cats;
-    // scratch: the cursor head, then each catalogue's prepared copies
-    std::vector<size_t> off(2 * nc);
-    size_t bytes = 256;
-    P->n_pad.assign(2 * nc, 0);
-    for (int m = 0; m < nc; ++m) {
-        const long long nd = P->cats[m].n_data, nr = P->cats[m].n_rand;
-        P->n_pad[2 * m] = round_up(nd, T);
-        P->n_pad[2 * m + 1] = round_up(nr, T);
-        off[2 * m] = bytes;
-        bytes += (prepare_bytes(nd, P->n_pad[2 * m], P->is_xyz) + 255) / 256 * 256;
-        off[2 * m + 1] = bytes;
-        bytes += (prepare_bytes(nr, P->n_pad[2 * m + 1], P->is_xyz) + 255) / 256 * 256;
+    const int nc = P->n_cats, nc2 = 2 * nc;
+    P->sm_count = sm_count;
+    P->n_pad.assign(nc2, 0);
+    P->src_off.assign(nc2 + 1, 0);
+    P->dst_off.assign(nc2 + 1, 0);
+    std::vector<BatchCat> hc(nc2);
+    for (int c = 0; c < nc2; ++c) {
+        const wtheta_catalog_pair& q = P->cats[c / 2];
+        hc[c].src = c % 2 ? q.rand : q.data;
+        hc[c].n = c % 2 ? q.n_rand : q.n_data;
+        P->n_pad[c] = round_up(hc[c].n, T);
+        P->src_off[c + 1] = P->src_off[c] + hc[c].n;
+        P->dst_off[c + 1] = P->dst_off[c] + P->n_pad[c];
     }
+    P->n_all = P->src_off[nc2];
+    P->n_all_pad = P->dst_off[nc2];
+    const long long N = P->n_all, NP = P->n_all_pad;
+    auto a256 = [](size_t b) { return (b + 255) / 256 * 256; };
+    // scratch: the cursor head, the catalogue table and offsets, the FP64
+    // array and labels, the sort, the FP32 copies and chunk spheres
+    size_t bytes = 256;
+    const size_t off_cats = bytes;
+    bytes += a256((size_t)nc2 * sizeof(BatchCat));
+    const size_t off_offs = bytes;
+    bytes += a256((size_t)2 * (nc2 + 1) * 8);
+    const size_t off_x = bytes;
+    bytes += a256((size_t)N * 24);
+    const size_t off_lab = bytes;
+    bytes += a256((size_t)N * 4);
+    const size_t off_sort = bytes;
+    bytes += a256(order_bytes(N, 1));
+    const size_t off_p32 = bytes;
+    bytes += a256((size_t)NP * 16);
+    const size_t off_c32 = bytes;
+    bytes += a256((size_t)NP / 32 * 16);
     if (P->scratch) cudaFree(P->scratch);
     P->scratch = nullptr;
     int rc = dev_malloc(&P->scratch, bytes);
     if (rc) return rc;
     unsigned char* base = (unsigned char*)P->scratch;
     P->d_cursor = (unsigned long long*)base;
-    P->prep.assign(2 * nc, Prepared());
-    for (int m = 0; m < nc; ++m) {
-        rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], P->is_xyz, 0,
-                     base + off[2 * m], sm_count, st, &P->prep[2 * m]);
-        if (!rc)
-            rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], P->is_xyz, 1,
-                         base + off[2 * m + 1], sm_count, st, &P->prep[2 * m + 1]);
-        if (rc) return rc;
+    P->d_cats = (BatchCat*)(base + off_cats);
+    P->d_src_off = (long long*)(base + off_offs);
+    P->x_all = (double*)(base + off_x);
+    P->lab_all = (int*)(base + off_lab);
+    P->sort_scratch = base + off_sort;
+    P->p32_all = (float4*)(base + off_p32);
+    P->c32_all = (float4*)(base + off_c32);
+    std::vector<long long> offs(P->src_off);
+    offs.insert(offs.end(), P->dst_off.begin(), P->dst_off.end());
+    rc = check_cuda(cudaMemcpyAsync(P->d_cats, hc.data(), sizeof(BatchCat) * nc2,
+                                    cudaMemcpyHostToDevice, st));
+    if (!rc) rc = check_cuda(cudaMemcpyAsync(P->d_src_off, offs.data(), offs.size() * 8,
+                                             cudaMemcpyHostToDevice, st));
+    if (rc) return rc;
+    // every catalogue's view of the shared copies (FP64 in the caller's order:
+    // the FP32 copies carry each point's position in the FP64 array)
+    P->prep.assign(nc2, Prepared());
+    for (int c = 0; c < nc2; ++c) {
+        Prepared& q = P->prep[c];
+        q.p32 = P->p32_all + P->dst_off[c];
+        q.c32 = P->c32_all + P->dst_off[c] / 32;
+        q.x64 = P->x_all;
+        q.stride = N;
+        q.sorted = 0;
     }
     // the work table: DD, DR, RR of every pair, biggest count first
     std::vector<Segment> segs;
@@ -2743,16 +2863,13 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
     P->caps.assign(2 * nc, nullptr);
     if ((rc = dev_malloc((void**)&P->d_segs, sizeof(Segment) * sorted.size()))) return rc;
     if (P->cull) {
-        // kept counters, total, the count table, every catalogue's tile caps,
-        // and one list of item indices per count
+        // kept counters, total, the count table, the tile caps of all the
+        // catalogues' tiles, and one list of item indices per count
         size_t cb = ((size_t)P->n_segs * 8 + 8 + 255) / 256 * 256;
         const size_t off_cs = cb;
         cb += (sizeof(CullSeg) * P->n_segs + 255) / 256 * 256;
-        std::vector<size_t> off_caps(2 * nc);
-        for (int c = 0; c < 2 * nc; ++c) {
-            off_caps[c] = cb;
-            cb += ((size_t)(P->n_pad[c] / T) * sizeof(TileCap) + 255) / 256 * 256;
-        }
+        const size_t off_caps = cb;
+        cb += ((size_t)(NP / T) * sizeof(TileCap) + 255) / 256 * 256;
         const size_t off_lists = cb;
         cb += (size_t)items * 4;
         if ((rc = dev_malloc(&P->cull_mem, cb))) return rc;
@@ -2760,7 +2877,8 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
         P->d_kept = (unsigned long long*)cm;
         P->d_total = P->d_kept + P->n_segs;
         P->d_cull = (CullSeg*)(cm + off_cs);
-        for (int c = 0; c < 2 * nc; ++c) P->caps[c] = (TileCap*)(cm + off_caps[c]);
+        P->caps_all = (TileCap*)(cm + off_caps);
+        for (int c = 0; c < nc2; ++c) P->caps[c] = P->caps_all + P->dst_off[c] / T;
         unsigned* lists = (unsigned*)(cm + off_lists);
         for (size_t i = 0; i < order.size(); ++i) {
             cull[i].ca = P->caps[seg_cat_a[order[i]]];
@@ -2771,8 +2889,12 @@ static int plan_layout(wtheta_plan* P, const Variant* v, int sm_count, cudaStrea
                                         cudaMemcpyHostToDevice, st));
         if (rc) return rc;
     }
-    return check_cuda(cudaMemcpyAsync(P->d_segs, sorted.data(), sizeof(Segment) * sorted.size(),
-                                      cudaMemcpyHostToDevice, st));
+    rc = check_cuda(cudaMemcpyAsync(P->d_segs, sorted.data(), sizeof(Segment) * sorted.size(),
+                                    cudaMemcpyHostToDevice, st));
+    // the catalogues, prepared once now (for the autotuner's timing); the
+    // graph prepares them again on every run
+    if (!rc) rc = batch_prepare(P, (int)T, st);
+    return rc;
 }
 
 static int launch_batch_pairs(wtheta_plan* P, const Variant* v, long long item_begin,
@@ -2842,26 +2964,12 @@ static int plan_capture(wtheta_plan* P, const DeviceInfo& di) {
     const unsigned long long launches0 = g_launches.load();
     rc = check_cuda(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     if (!rc) {
-        // re-prepare every catalogue from its current coordinates, then count
-        unsigned char* base = (unsigned char*)P->scratch;
-        for (int m = 0; m < P->n_cats && !rc; ++m) {
-            Prepared a, b;
-            const size_t off_a = (size_t)((const unsigned char*)P->prep[2 * m].p32 - base);
-            const size_t off_b = (size_t)((const unsigned char*)P->prep[2 * m + 1].p32 - base);
-            rc = prepare(P->cats[m].data, P->cats[m].n_data, P->n_pad[2 * m], P->is_xyz, 0,
-                         base + off_a, di.sm_count, cs, &a);
-            if (!rc)
-                rc = prepare(P->cats[m].rand, P->cats[m].n_rand, P->n_pad[2 * m + 1], P->is_xyz, 1,
-                             base + off_b, di.sm_count, cs, &b);
-        }
+        // re-prepare every catalogue from its current coordinates (one
+        // pipeline over all of them, tile caps included), then count
+        const int T = P->v->nt * P->v->r;
+        rc = batch_prepare(P, T, cs);
         if (!rc && P->cull) {
-            // tile caps of every catalogue, the kept tile pairs of every count,
-            // and the launch's item ranges
-            const int T = P->v->nt * P->v->r;
-            for (int c = 0; c < 2 * P->n_cats && !rc; ++c) {
-                const long long n = c % 2 ? P->cats[c / 2].n_rand : P->cats[c / 2].n_data;
-                rc = launch_tile_caps(P->prep[c].p32, n, T, P->n_pad[c] / T, P->caps[c], cs);
-            }
+            // the kept tile pairs of every count, and the launch's item ranges
             if (!rc) rc = check_cuda(cudaMemsetAsync(P->d_kept, 0, (size_t)P->n_segs * 8, cs));
             if (!rc) {
                 k_cull_batch<<<launch_grid(P->total_items, di.sm_count), 256, 0, cs>>>(
@@ -2916,7 +3024,9 @@ static void plan_release(wtheta_plan* P) {
 static int batch_plan_impl(const wtheta_catalog_pair* cats, int n_cats, int is_xyz,
                            const double* edges, int K, const wtheta_tune* tune, cudaStream_t st,
                            wtheta_plan** out) {
-    if (!out || !cats || n_cats < 1 || (is_xyz != 0 && is_xyz != 1)) return WTHETA_EINVAL;
+    // catalogues are labelled by 16-bit index in the shared sort
+    if (!out || !cats || n_cats < 1 || n_cats > 32768 || (is_xyz != 0 && is_xyz != 1))
+        return WTHETA_EINVAL;
     for (int m = 0; m < n_cats; ++m) {
         const wtheta_catalog_pair& c = cats[m];
         if (c.n_data < 2 || c.n_rand < 2 || !c.data || !c.rand) return WTHETA_EINVAL;

@@ -149,7 +149,7 @@ int launch_pairs(const Variant* v, const PairParams& prm, int grid, size_t smem,
 int launch_finalize_segments(const Segment* d_segs, int n_segs, int K, cudaStream_t st);
 // Spatial order of n FP64 points (SoA, stride): *order = original indices
 // sorted by Hilbert key, or by (label, key) when labels (device, values in
-// [0, n_labels), n_labels <= 256) are given; *sorted_labels (optional) then
+// [0, n_labels), n_labels <= 65536) are given; *sorted_labels (optional) then
 // receives the labels in that order.  scratch: order_bytes(n, labels != 0).
 size_t order_bytes(long long n, int with_labels);
 int spatial_order(const double* x64, long long stride, long long n, int check,

@@ -117,3 +117,39 @@ def test_batch_shapes_agree(W, tune):
     W.wtheta_batch_run(plan, b)
     torch.cuda.synchronize()
     assert torch.equal(a, b)
+
+
+def test_batch_beyond_2_to_the_24_points(W):
+    """Catalogues that start more than 2^24 points into the plan's shared
+    arrays (their padding sentinels must stay distinct in FP32) count exactly:
+    the last mocks of a plan holding ~19M points equal the oracle."""
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    K = len(e) - 1
+    rng = np.random.default_rng(35)
+    fill = []
+    for m in range(62):  # 62 x 300k uniform points ahead of the checked mocks
+        ra0, dec0 = rng.uniform(0, 360), rng.uniform(-60, 45)
+        fp = synth.Patch(ra0, 15.0, dec0, dec0 + 15.0)
+        fill.append((synth.uniform(fp, 150_001 + m, 35, "test", "data", m),
+                     synth.uniform(fp, 149_999, 35, "test", "random", m)))
+    tail = _mocks(2, 3000, 9000, 36)
+    mocks = fill + tail
+    dev = [(torch.from_numpy(d).cuda(), torch.from_numpy(r).cuda()) for d, r in mocks]
+    assert sum(len(d) + len(r) for d, r in mocks) // 2 > (1 << 24)
+    plan = W.wtheta_batch_plan(dev, e, tune=dict(threads=128, points_per_thread=8))
+    out = torch.zeros((len(mocks), 3, K + 2), dtype=torch.int64, device="cuda")
+    W.wtheta_batch_run(plan, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.uint64)
+    W.wtheta_batch_free(plan)
+    for i, (d, r) in enumerate(tail):
+        D, R = O.radec_to_xyz(d), O.radec_to_xyz(r)
+        for k, (A, B, auto) in enumerate([(D, None, True), (D, R, False), (R, None, True)]):
+            want = O.count_xyz(A, B, e, auto)
+            amb = O.count_ambiguous_xyz(A, B, e, auto)
+            g = got[len(fill) + i, k]
+            assert int(g.sum()) == int(want.sum())
+            if amb == 0:
+                assert np.array_equal(g, want), (i, k)
+            else:
+                assert np.abs(g.astype(np.int64) - want.astype(np.int64)).sum() <= 2 * amb
