@@ -182,7 +182,9 @@ typedef struct wtheta_tune {
     int32_t blocks_per_sm;     /* resident blocks per SM the grid is sized for */
     int32_t skip_far;          /* 1: skip tile pairs that bounding caps show to lie
                                   wholly beyond the top edge (exact: their pairs are
-                                  overflow); 2: evaluate every tile pair          */
+                                  overflow); 2: evaluate every tile pair; 0: skip
+                                  when the tile pairs fill more than two waves of
+                                  the launch                                      */
     int32_t span_bins;         /* 1: settle a thread's A points against a chunk of
                                   32 B points in one slot, or by one compare per pair
                                   against a single edge, when the bounding spheres

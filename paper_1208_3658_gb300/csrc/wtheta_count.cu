@@ -244,8 +244,8 @@ __device__ __forceinline__ unsigned cell_key(double x, double y, double z, int L
 // Spatial order of a catalogue: a 31-bit key per point (cube-map face, then
 // the Hilbert index of its cell on a 2^14 x 2^14 grid of the face, cells of
 // about 20 arcsec), sorted by a stable least-significant-digit radix sort
-// (4 passes of 8 bits: per-block digit counts, one exclusive scan, a stable
-// scatter).  Consecutive points of the order are then close on the sky down
+// (4 passes of 8 bits: per-block digit counts, a scan of each digit's counts
+// across the blocks, a stable scatter).  Consecutive points of the order are then close on the sky down
 // to the scale of a few points, which the per-tile culling and the
 // per-chunk settling of pairs both rely on.
 constexpr int kSortLevel = 14;
@@ -284,17 +284,59 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_hist(const unsigned* __r
     hist[(long long)t * gridDim.x + blockIdx.x] = cnt[t];
 }
 
-// Stable scatter of one pass: block b writes its keys of digit d from
-// offs[d * n_blocks + b] on, in index order (rounds of 256 keys; inside a
-// round, warps in order and lanes in order).
+// Per digit d, the keys of digit d in blocks before b: hist[d * n_blocks + b]
+// becomes that count (an exclusive scan along the digit's row, which is
+// contiguous: coalesced), and tot[d] the digit's total.  One warp per digit,
+// 8 digits per block of 256 threads.
+__global__ void __launch_bounds__(256) k_digit_rows(unsigned* __restrict__ hist, int n_blocks,
+                                                    unsigned* __restrict__ tot) {
+    const int lane = threadIdx.x & 31;
+    const int d = blockIdx.x * 8 + (threadIdx.x >> 5);
+    unsigned* row = hist + (long long)d * n_blocks;
+    unsigned run = 0;
+#pragma unroll 4
+    for (int b0 = 0; b0 < n_blocks; b0 += 32) {
+        const int b = b0 + lane;
+        const unsigned v = b < n_blocks ? row[b] : 0u;
+        unsigned incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (b < n_blocks) row[b] = run + incl - v;
+        run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) tot[d] = run;
+}
+
+// Stable scatter of one pass: block b writes its keys of digit d from the
+// keys of smaller digits (the exclusive scan of tot, done here by every
+// block) plus rows[d * n_blocks + b] (k_digit_rows) on, in index order
+// (rounds of 256 keys; inside a round, warps in order and lanes in order).
 __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
     const unsigned* __restrict__ key_in, const unsigned* __restrict__ idx_in, long long n,
-    int shift, int rounds, const unsigned* __restrict__ offs, unsigned* __restrict__ key_out,
-    unsigned* __restrict__ idx_out) {
+    int shift, int rounds, const unsigned* __restrict__ rows, const unsigned* __restrict__ tot,
+    unsigned* __restrict__ key_out, unsigned* __restrict__ idx_out) {
+    static_assert(kSortThreads == 256, "one thread per digit");
     __shared__ unsigned base[256];
     __shared__ unsigned wcnt[kSortThreads / 32][256];
+    __shared__ unsigned wsum[kSortThreads / 32];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    base[t] = offs[(long long)t * gridDim.x + blockIdx.x];
+    {
+        const unsigned x = tot[t];
+        unsigned incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[w] = incl;
+        __syncthreads();
+        unsigned pre = incl - x;
+        for (int q = 0; q < w; ++q) pre += wsum[q];
+        base[t] = pre + rows[(long long)t * gridDim.x + blockIdx.x];
+    }
     const long long lo = blockIdx.x * (long long)kSortThreads * rounds;
     for (int r = 0; r < rounds; ++r) {
 #pragma unroll
@@ -328,51 +370,71 @@ __global__ void __launch_bounds__(kSortThreads) k_digit_scatter(
     }
 }
 
-// Exclusive prefix sum in place (one block of 1024).  Up to kScanStage
-// values are first staged in shared memory by coalesced loads (each thread
-// then scans a contiguous run of them there); longer arrays are read in place.
-constexpr int kScanStage = 8192;
-__global__ void __launch_bounds__(1024) k_exclusive_scan(unsigned* __restrict__ a, int n) {
-    __shared__ unsigned warp_sum[32];
-    __shared__ unsigned stage[kScanStage];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const bool staged = n <= kScanStage;
-    if (staged) {
-        for (int i = t; i < n; i += 1024) stage[i] = a[i];
-        __syncthreads();
-    }
-    unsigned* v = staged ? stage : a;
-    const int per = (n + 1023) / 1024;
-    const int lo = min(t * per, n), hi = min(lo + per, n);
-    unsigned sum = 0;
-    for (int i = lo; i < hi; ++i) sum += v[i];
-    unsigned incl = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) warp_sum[w] = incl;
-    __syncthreads();
-    if (w == 0) {
-        unsigned ws = warp_sum[lane];
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned v = __shfl_up_sync(0xffffffffu, ws, o);
-            if (lane >= o) ws += v;
+// The one or two catalogues of a count, prepared together: both into one
+// FP64 SoA array x (stride N = na + nb), converted from RA/Dec or copied from
+// unit vectors (then checked), each point with its sort key (the cell key,
+// with the catalogue in bit 31 so that b's points sort after a's) and its
+// position.  FP64 work: launched in blocks of 64 threads, so that a small
+// catalogue still spreads over every SM.
+__global__ void __launch_bounds__(64) k_joint_keys(const double* __restrict__ a, long long na,
+                                                   const double* __restrict__ b, long long nb,
+                                                   int is_xyz, double* __restrict__ x,
+                                                   unsigned* __restrict__ key,
+                                                   unsigned* __restrict__ idx) {
+    const long long N = na + nb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        const bool in_b = i >= na;
+        const double* src = in_b ? b : a;
+        const long long j = in_b ? i - na : i, n = in_b ? nb : na;
+        double px, py, pz;
+        if (is_xyz) {
+            px = src[j];
+            py = src[n + j];
+            pz = src[2 * n + j];
+            check_unit(px, py, pz);
+        } else {
+            radec_unit(src[2 * j], src[2 * j + 1], px, py, pz);
         }
-        warp_sum[lane] = ws;  // inclusive over warps
+        x[i] = px;
+        x[N + i] = py;
+        x[2 * N + i] = pz;
+        key[i] = cell_key(px, py, pz, kSortLevel) | (in_b ? 0x80000000u : 0u);
+        idx[i] = (unsigned)i;
     }
-    __syncthreads();
-    unsigned run = incl - sum + (w > 0 ? warp_sum[w - 1] : 0u);
-    for (int i = lo; i < hi; ++i) {
-        const unsigned c = v[i];
-        v[i] = run;
-        run += c;
-    }
-    if (staged) {
-        __syncthreads();
-        for (int i = t; i < n; i += 1024) a[i] = stage[i];
+}
+
+// FP32 and FP64 copies of both catalogues in the joint order (order: the
+// sorted positions of x, a's points first): a's at [0, na) with sentinels up
+// to pa, b's at [pa, pa + nb) with sentinels up to pa + pb (tags 0 and 1); the
+// FP64 copy has stride pa + pb, and each FP32 point keeps in w its index
+// within its own catalogue.
+__global__ void k_gather_joint(const double* __restrict__ x, long long na, long long pa,
+                               long long nb, long long pb, const unsigned* __restrict__ order,
+                               float4* __restrict__ p32, double* __restrict__ s64) {
+    const long long N = na + nb, P = pa + pb;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
+         i += (long long)gridDim.x * blockDim.x) {
+        const bool in_b = i >= pa;
+        const long long j = in_b ? i - pa : i, n = in_b ? nb : na;
+        double px, py, pz;
+        float4 q;
+        if (j < n) {
+            const long long k = order[(in_b ? na : 0) + j];
+            px = x[k];
+            py = x[N + k];
+            pz = x[2 * N + k];
+            q = point32(px, py, pz, in_b ? k - na : k);
+        } else {
+            q = sentinel32(in_b ? 1 : 0, j - n);
+            px = q.x;
+            py = q.y;
+            pz = q.z;
+        }
+        p32[i] = q;
+        s64[i] = px;
+        s64[P + i] = py;
+        s64[2 * P + i] = pz;
     }
 }
 
@@ -1776,6 +1838,27 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
     }
 }
 
+// The device tables of a w(theta) launch (its counts' segments and culling
+// table), written by one small kernel from its parameters, which also zeroes
+// n0 words at z0 and n1 at z1 (the launch cursor and the kept counters).
+struct CountTables {
+    Segment segs[3];
+    CullSeg cs[3];
+    int n_segs;
+    int with_cull;
+};
+__global__ void k_set_tables(const CountTables t, Segment* __restrict__ segs,
+                             CullSeg* __restrict__ cs, unsigned long long* __restrict__ z0, int n0,
+                             unsigned long long* __restrict__ z1, int n1) {
+    const int i = threadIdx.x;
+    if (i < t.n_segs) {
+        segs[i] = t.segs[i];
+        if (t.with_cull) cs[i] = t.cs[i];
+    }
+    if (i < n0) z0[i] = 0ull;
+    if (i < n1) z1[i] = 0ull;
+}
+
 // counts[K+1] = total - sum(counts[0..K]) for every count of a batch.
 __global__ void k_finalize_segments(const Segment* __restrict__ segs, int n_segs, int K) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_segs; i += gridDim.x * blockDim.x) {
@@ -1943,51 +2026,81 @@ static long long sort_blocks(long long n) {
 size_t order_bytes(long long n, int with_labels) {
     const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
     return (4 + (with_labels ? 1 : 0)) * a4 +                   // keys, indices (x2), labels
-           ((size_t)sort_blocks(n) * 256 * 4 + 255) / 256 * 256;  // digit counts per block
+           ((size_t)sort_blocks(n) * 256 * 4 + 255) / 256 * 256 +  // digit counts per block
+           256 * 4;                                              // digit totals
+}
+
+// The buffers of a sort's scratch (order_bytes(n, with_labels) bytes): keys
+// and indices twice (passes alternate), labels, per-block digit counts and
+// the digit totals.
+struct SortBufs {
+    unsigned* key[2];
+    unsigned* idx[2];
+    unsigned* lab;
+    unsigned* hist;
+    unsigned* tot;
+    long long G;
+    int rounds;
+};
+static SortBufs sort_bufs(unsigned char* scratch, long long n, int with_labels) {
+    const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
+    SortBufs B;
+    B.G = sort_blocks(n);
+    B.rounds = sort_rounds(n);
+    B.key[0] = (unsigned*)scratch;
+    B.key[1] = (unsigned*)(scratch + a4);
+    B.idx[0] = (unsigned*)(scratch + 2 * a4);
+    B.idx[1] = (unsigned*)(scratch + 3 * a4);
+    B.lab = (unsigned*)(scratch + 4 * a4);
+    B.hist = (unsigned*)(scratch + (4 + (with_labels ? 1 : 0)) * a4);
+    B.tot = B.hist + ((size_t)B.G * 256 + 63) / 64 * 64;
+    return B;
+}
+
+// One stable pass on the byte of key_in at shift.
+static void digit_pass(const SortBufs& B, const unsigned* key_in, const unsigned* idx_in,
+                       long long n, int shift, unsigned* key_out, unsigned* idx_out,
+                       cudaStream_t st) {
+    k_digit_hist<<<(unsigned)B.G, kSortThreads, 0, st>>>(key_in, n, shift, B.rounds, B.hist);
+    k_digit_rows<<<256 / 8, 256, 0, st>>>(B.hist, (int)B.G, B.tot);
+    k_digit_scatter<<<(unsigned)B.G, kSortThreads, 0, st>>>(key_in, idx_in, n, shift, B.rounds,
+                                                            B.hist, B.tot, key_out, idx_out);
+    count_launch(3);
+}
+
+// The four passes over 32-bit keys in B.key[0] (indices in B.idx[0]); the
+// sorted keys and indices come back in the same buffers.
+static void key_passes(const SortBufs& B, long long n, cudaStream_t st) {
+    for (int pass = 0; pass < 4; ++pass) {
+        const int in = pass & 1, o = in ^ 1;
+        digit_pass(B, B.key[in], B.idx[in], n, 8 * pass, B.key[o], B.idx[o], st);
+    }
 }
 
 int spatial_order(const double* x64, long long stride, long long n, int check,
                   const int* labels, int n_labels, unsigned char* scratch, int sm_count,
                   cudaStream_t st, const unsigned** order, const unsigned** sorted_labels) {
-    const size_t a4 = ((size_t)n * 4 + 255) / 256 * 256;
-    const long long G = sort_blocks(n);
-    const int rounds = sort_rounds(n);
-    unsigned* key[2] = {(unsigned*)scratch, (unsigned*)(scratch + a4)};
-    unsigned* idx[2] = {(unsigned*)(scratch + 2 * a4), (unsigned*)(scratch + 3 * a4)};
-    unsigned* lab = (unsigned*)(scratch + 4 * a4);
-    unsigned* hist = (unsigned*)(scratch + (4 + (labels ? 1 : 0)) * a4);
-    *order = idx[0];
+    const SortBufs B = sort_bufs(scratch, n, labels != nullptr);
+    *order = B.idx[0];
     if (sorted_labels) *sorted_labels = nullptr;
     if (n <= 0) return WTHETA_OK;
-    k_sort_keys<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, check, key[0], idx[0]);
+    k_sort_keys<<<launch_grid(n, sm_count), 256, 0, st>>>(x64, stride, n, check, B.key[0],
+                                                          B.idx[0]);
     count_launch();
-    for (int pass = 0; pass < 4; ++pass) {
-        const int in = pass & 1, o = in ^ 1;
-        k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], n, 8 * pass, rounds, hist);
-        k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
-        k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(key[in], idx[in], n, 8 * pass, rounds,
-                                                              hist,
-                                                              key[o], idx[o]);
-        count_launch(3);
-    }
-    // four passes: the order is back in the first buffers
+    key_passes(B, n, st);
     if (labels) {
         // one more stable pass per byte of the label (two above 256 labels):
         // regions in label order, each in spatial order
         int cur = 0;
         for (int shift = 0; shift == 0 || (shift < 16 && (n_labels - 1) >> shift); shift += 8) {
-            k_sorted_labels<<<launch_grid(n, sm_count), 256, 0, st>>>(idx[cur], labels, n, n_labels,
-                                                                      lab);
-            k_digit_hist<<<(unsigned)G, kSortThreads, 0, st>>>(lab, n, shift, rounds, hist);
-            k_exclusive_scan<<<1, 1024, 0, st>>>(hist, (int)(G * 256));
-            k_digit_scatter<<<(unsigned)G, kSortThreads, 0, st>>>(lab, idx[cur], n, shift, rounds,
-                                                                  hist, key[cur ^ 1],
-                                                                  idx[cur ^ 1]);
-            count_launch(4);
+            k_sorted_labels<<<launch_grid(n, sm_count), 256, 0, st>>>(B.idx[cur], labels, n,
+                                                                      n_labels, B.lab);
+            count_launch();
+            digit_pass(B, B.lab, B.idx[cur], n, shift, B.key[cur ^ 1], B.idx[cur ^ 1], st);
             cur ^= 1;
         }
-        *order = idx[cur];
-        if (sorted_labels) *sorted_labels = key[cur];
+        *order = B.idx[cur];
+        if (sorted_labels) *sorted_labels = B.key[cur];
     }
     return check_cuda(cudaGetLastError());
 }
@@ -2034,6 +2147,57 @@ int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int 
     out->x64 = s64;
     out->stride = n_pad;
     out->sorted = 1;
+    return check_cuda(cudaGetLastError());
+}
+
+size_t prepare_joint_bytes(long long na, long long pa, long long nb, long long pb) {
+    const long long N = na + nb, P = pa + pb;
+    size_t b = ((size_t)P * 16 + 255) / 256 * 256;       // FP32 points
+    b += ((size_t)P / 32 * 16 + 255) / 256 * 256;        // chunk bounding spheres
+    b += ((size_t)P * 24 + 255) / 256 * 256;             // FP64, spatial order
+    b += ((size_t)N * 24 + 255) / 256 * 256;             // FP64, input order
+    b += order_bytes(N, 0);                              // the sort
+    return b;
+}
+
+int prepare_joint(const double* a, long long na, long long pa, const double* b, long long nb,
+                  long long pb, int is_xyz, unsigned char* scratch, int sm_count, cudaStream_t st,
+                  Prepared* A, Prepared* B) {
+    TraceRange trace("prepare");
+    const long long N = na + nb, P = pa + pb;
+    if (N >= (1LL << 32) - 1) return WTHETA_EINVAL;  // 32-bit positions in the sort
+    unsigned char* sp = scratch;
+    float4* p32 = (float4*)sp;
+    sp += ((size_t)P * 16 + 255) / 256 * 256;
+    float4* c32 = (float4*)sp;
+    sp += ((size_t)P / 32 * 16 + 255) / 256 * 256;
+    double* s64 = (double*)sp;
+    sp += ((size_t)P * 24 + 255) / 256 * 256;
+    double* x = (double*)sp;
+    sp += ((size_t)N * 24 + 255) / 256 * 256;
+    const SortBufs S = sort_bufs(sp, N, 0);
+    if (N > 0) {
+        const long long g = std::min<long long>((N + 63) / 64, (long long)sm_count * 32);
+        k_joint_keys<<<(unsigned)g, 64, 0, st>>>(a, na, b, nb, is_xyz, x, S.key[0], S.idx[0]);
+        count_launch();
+        key_passes(S, N, st);
+    }
+    if (P > 0) {
+        k_gather_joint<<<launch_grid(P, sm_count), 256, 0, st>>>(x, na, pa, nb, pb, S.idx[0], p32,
+                                                                 s64);
+        k_chunk_caps<<<launch_grid(P, sm_count), 256, 0, st>>>(p32, P, P, c32);
+        count_launch(2);
+    }
+    A->p32 = p32;
+    A->c32 = c32;
+    A->x64 = s64;
+    A->stride = P;
+    A->sorted = 1;
+    B->p32 = p32 + pa;
+    B->c32 = c32 + pa / 32;
+    B->x64 = s64 + pa;
+    B->stride = P;
+    B->sorted = 1;
     return check_cuda(cudaGetLastError());
 }
 
@@ -2180,56 +2344,52 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     const long long T = (long long)v->nt * v->r;  // TA == TB
     const long long pa = round_up(n_a, T), pb = is_auto ? pa : round_up(n_b, T);
 
-    // scratch: the cursor, then each catalogue's prepared copies
-    const size_t ba = prepare_bytes(n_a, pa, is_xyz);
-    const size_t bb = is_auto ? 0 : prepare_bytes(n_b, pb, is_xyz);
+    const long long ta = pa / T, tb = pb / T;
+    const long long n_items = is_auto ? ta * (ta + 1) / 2 : ta * tb;
+    const size_t smem = v->smem(K, tab.n_lut);
+    const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
+    int resident = 0;  // blocks resident at once
+    if ((rc = grid_for(v, smem, 1LL << 40, di.sm_count, want_per_sm, &resident))) return rc;
+    // skip tile pairs wholly beyond the top edge (their pairs are overflow),
+    // unless the items fill at most two waves of the launch: the caps and the
+    // culling launches then cost about what they could save
+    const bool skip_far = (!tune || tune->skip_far != 2) && edges[K] < 180.0 && n_items > 0 &&
+                          n_items < (1LL << 32) &&
+                          (n_items > 2LL * resident || (tune && tune->skip_far == 1));
+
+    // scratch: the cursor and the kept count, both catalogues prepared
+    // together, then the tile caps and the kept list
+    const size_t bp = prepare_joint_bytes(n_a, pa, is_auto ? 0 : n_b, is_auto ? 0 : pb);
+    const size_t off_caps = 256 + (bp + 255) / 256 * 256;
+    const size_t off_list = off_caps + (skip_far ? ((size_t)(ta + tb) * sizeof(TileCap) + 255) / 256 * 256 : 0);
+    const size_t bytes = off_list + (skip_far ? (size_t)n_items * 4 : 0);
     void* scratch = nullptr;
-    void* cull_scratch = nullptr;
-    if ((rc = dev_malloc_async(&scratch, 256 + ba + bb, st))) return rc;
+    if ((rc = dev_malloc_async(&scratch, bytes, st))) return rc;
     unsigned char* sp = (unsigned char*)scratch;
     unsigned long long* cursor = (unsigned long long*)sp;
     Prepared A, B;
-    rc = prepare(ca, n_a, pa, is_xyz, 0, sp + 256, di.sm_count, st, &A);
-    if (!rc && !is_auto) rc = prepare(cb, n_b, pb, is_xyz, 1, sp + 256 + ba, di.sm_count, st, &B);
+    rc = prepare_joint(ca, n_a, pa, is_auto ? nullptr : cb, is_auto ? 0 : n_b, is_auto ? 0 : pb,
+                       is_xyz, sp + 256, di.sm_count, st, &A, &B);
     if (is_auto) B = A;
-    if (!rc) rc = check_cuda(cudaMemsetAsync(cursor, 0, sizeof(unsigned long long), st));
+    if (!rc) rc = check_cuda(cudaMemsetAsync(cursor, 0, 2 * sizeof(unsigned long long), st));
 
-    const long long ta = pa / T, tb = pb / T;
-    const long long n_items = is_auto ? ta * (ta + 1) / 2 : ta * tb;
-    // skip tile pairs wholly beyond the top edge (their pairs are overflow)
-    const bool skip_far = (!tune || tune->skip_far != 2) && edges[K] < 180.0 && n_items > 0 &&
-                          n_items < (1LL << 32);
     unsigned* list = nullptr;
     unsigned long long* n_list = nullptr;
     if (!rc && skip_far) {
-        const size_t cull_bytes = 256 + (size_t)(ta + tb) * sizeof(TileCap) + (size_t)n_items * 4;
-        void* cs = nullptr;
-        rc = dev_malloc_async(&cs, cull_bytes, st);
-        if (!rc) {
-            cull_scratch = cs;
-            n_list = (unsigned long long*)cs;
-            TileCap* caps_a = (TileCap*)((unsigned char*)cs + 256);
-            TileCap* caps_b = is_auto ? caps_a : caps_a + ta;
-            list = (unsigned*)(caps_a + ta + tb);
-            rc = check_cuda(cudaMemsetAsync(n_list, 0, 8, st));
-            if (!rc) {
-                k_tile_caps<<<(unsigned)ta, 128, 0, st>>>(A.p32, n_a, (int)T, caps_a);
-                count_launch();
-                if (!is_auto) {
-                    k_tile_caps<<<(unsigned)tb, 128, 0, st>>>(B.p32, n_b, (int)T, caps_b);
-                    count_launch();
-                }
-                const double theta_top = edges[K] * (3.14159265358979323846 / 180.0);
-                k_cull_items<<<launch_grid(n_items, di.sm_count), 256, 0, st>>>(
-                    caps_a, caps_b, ta, tb, is_auto, n_items, theta_top, list, n_list, stats);
-                count_launch();
-                rc = check_cuda(cudaGetLastError());
-            }
-        }
+        n_list = cursor + 1;
+        TileCap* caps_a = (TileCap*)(sp + off_caps);
+        TileCap* caps_b = is_auto ? caps_a : caps_a + ta;
+        list = (unsigned*)(sp + off_list);
+        // one launch over both catalogues (b's tiles follow a's)
+        k_tile_caps<<<(unsigned)(is_auto ? ta : ta + tb), 128, 0, st>>>(A.p32, is_auto ? pa : pa + pb,
+                                                                     (int)T, caps_a);
+        const double theta_top = edges[K] * (3.14159265358979323846 / 180.0);
+        k_cull_items<<<launch_grid(n_items, di.sm_count), 256, 0, st>>>(
+            caps_a, caps_b, ta, tb, is_auto, n_items, theta_top, list, n_list, stats);
+        count_launch(2);
+        rc = check_cuda(cudaGetLastError());
     }
-    const size_t smem = v->smem(K, tab.n_lut);
     int grid = 0;
-    const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
     if (!rc) rc = grid_for(v, smem, n_items, di.sm_count, want_per_sm, &grid);
     if (!rc) {
         Segment seg = make_segment(A, B, ta, tb, is_auto, 0, counts, total);
@@ -2246,17 +2406,11 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
             rc = check_cuda(cudaGetLastError());
         }
     }
-    cudaError_t fe = cudaFreeAsync(scratch, st);
+    const cudaError_t fe = cudaFreeAsync(scratch, st);
     if (!rc) rc = check_cuda(fe);
-    if (cull_scratch) {
-        fe = cudaFreeAsync(cull_scratch, st);
-        if (!rc) rc = check_cuda(fe);
-    }
     return rc;
 }
 
-// Pairs (i < j) of an auto count of n points whose first point i is in the
-// sorted rows [r0, r1).
 // Pairs (i < j) of an auto count of n points whose first point i is in the
 // sorted rows [r0, r1).
 static unsigned long long auto_pairs_in_rows(long long n, long long r0, long long r1) {
@@ -2328,16 +2482,23 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     const int n_segs = (int)cnts.size();
     long long total_items = 0;
     for (const Cnt& c : cnts) total_items += c.items;
+    const size_t smem = v->smem(K, tab.n_lut);
+    const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
+    int resident = 0;  // blocks resident at once
+    if ((rc = grid_for(v, smem, 1LL << 40, di.sm_count, want_per_sm, &resident))) return rc;
+    // skip far tile pairs unless the items fill at most two waves of the
+    // launch (the caps and the culling launches then cost about what they
+    // could save) or a shard split needs the kept items per row
     const bool cull = (!tune || tune->skip_far != 2) && edges[K] < 180.0 && td * td < (1LL << 32) &&
-                      td * tr < (1LL << 32) && tr * tr < (1LL << 32);
+                      td * tr < (1LL << 32) && tr * tr < (1LL << 32) &&
+                      (total_items > 2LL * resident || n_shards > 1 || (tune && tune->skip_far == 1));
     // scratch: cursor and kept total, segments, culling table, kept counts,
-    // both prepared catalogues, tile caps, kept lists (and kept items per row)
-    const size_t ba = prepare_bytes(nd, pd, is_xyz), bb = prepare_bytes(nr, pr, is_xyz);
+    // both catalogues prepared together, tile caps, kept lists (and kept
+    // items per row)
+    const size_t bp = prepare_joint_bytes(nd, pd, nr, pr);
     size_t bytes = 256 + 1024 + 1024 + 256;
-    const size_t off_d = bytes;
-    bytes += (ba + 255) / 256 * 256;
-    const size_t off_r = bytes;
-    bytes += (bb + 255) / 256 * 256;
+    const size_t off_prep = bytes;
+    bytes += (bp + 255) / 256 * 256;
     const size_t off_caps = bytes;
     if (cull) bytes += ((size_t)(td + tr) * sizeof(TileCap) + 255) / 256 * 256;
     const size_t off_rows = bytes;
@@ -2353,14 +2514,11 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     unsigned long long* d_kept = (unsigned long long*)(m + 256 + 2048);
     static_assert(3 * sizeof(Segment) <= 1024 && 3 * sizeof(CullSeg) <= 1024, "tables fit");
     Prepared D, R;
-    rc = prepare(cd, nd, pd, is_xyz, 0, m + off_d, di.sm_count, st, &D);
-    if (!rc) rc = prepare(cr, nr, pr, is_xyz, 1, m + off_r, di.sm_count, st, &R);
+    rc = prepare_joint(cd, nd, pd, cr, nr, pr, is_xyz, m + off_prep, di.sm_count, st, &D, &R);
     TileCap* caps_d = (TileCap*)(m + off_caps);
-    TileCap* caps_r = caps_d + td;
-    if (!rc && (cull || n_shards > 1)) {
-        rc = launch_tile_caps(D.p32, nd, (int)T, td, caps_d, st);
-        if (!rc) rc = launch_tile_caps(R.p32, nr, (int)T, tr, caps_r, st);
-    }
+    TileCap* caps_r = caps_d + td;  // R's tiles follow D's in the joint copies
+    if (!rc && (cull || n_shards > 1) && td + tr > 0)
+        rc = launch_tile_caps(D.p32, pd + pr, (int)T, td + tr, caps_d, st);
     const double theta_top = edges[K] * (3.14159265358979323846 / 180.0);
     auto cull_seg = [&](int i, long long begin) {
         const int k = cnts[i].kind;
@@ -2437,20 +2595,23 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
         item += cnts[i].items;
     }
     if (!rc && n_segs > 0) {
-        rc = check_cuda(cudaMemcpyAsync(d_segs, segs, sizeof(Segment) * n_segs,
-                                        cudaMemcpyHostToDevice, st));
-        if (!rc) rc = check_cuda(cudaMemsetAsync(m, 0, 16, st));
-        if (!rc && cull) {
-            rc = check_cuda(cudaMemcpyAsync(d_cull, cs, sizeof(CullSeg) * n_segs,
-                                            cudaMemcpyHostToDevice, st));
-            if (!rc) rc = check_cuda(cudaMemsetAsync(d_kept, 0, 3 * 8, st));
-            if (!rc)
-                rc = launch_cull_batch(d_cull, n_segs, total_items, theta_top, d_kept, d_segs,
-                                       n_kept, di.sm_count, st, stats);
+        // the segments and culling table, cursor and kept counters zeroed: one
+        // small launch instead of copies from pageable memory and memsets
+        CountTables tbl;
+        std::memset(&tbl, 0, sizeof(tbl));
+        for (int i = 0; i < n_segs; ++i) {
+            tbl.segs[i] = segs[i];
+            tbl.cs[i] = cs[i];
         }
-        const size_t smem = v->smem(K, tab.n_lut);
+        tbl.n_segs = n_segs;
+        tbl.with_cull = cull ? 1 : 0;
+        k_set_tables<<<1, 32, 0, st>>>(tbl, d_segs, d_cull, cursor, 2, d_kept, cull ? 3 : 0);
+        count_launch();
+        rc = check_cuda(cudaGetLastError());
+        if (!rc && cull)
+            rc = launch_cull_batch(d_cull, n_segs, total_items, theta_top, d_kept, d_segs, n_kept,
+                                   di.sm_count, st, stats);
         int grid = 0;
-        const int want_per_sm = tune && tune->blocks_per_sm ? tune->blocks_per_sm : 0;
         if (!rc) rc = grid_for(v, smem, std::max(total_items, 1LL), di.sm_count, want_per_sm, &grid);
         if (!rc && total_items > 0) {
             PairParams prm = make_params(v, tab, nullptr, d_segs, n_segs, 0, total_items, cursor,

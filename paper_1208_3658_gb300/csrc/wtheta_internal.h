@@ -138,6 +138,15 @@ int check_cuda(cudaError_t e);
 size_t prepare_bytes(long long n, long long n_pad, int is_xyz);
 int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int tag,
             unsigned char* scratch, int sm_count, cudaStream_t st, Prepared* out);
+// The one or two catalogues of a count prepared together (b absent: nb = pb
+// = 0): one conversion and key launch, one sort of the na + nb points, one
+// gather into FP32 and FP64 copies with a's points at [0, pa) and b's at
+// [pa, pa + pb) (each catalogue tile-padded with sentinels), one launch for
+// the chunk spheres of both.  scratch: prepare_joint_bytes(na, pa, nb, pb).
+size_t prepare_joint_bytes(long long na, long long pa, long long nb, long long pb);
+int prepare_joint(const double* a, long long na, long long pa, const double* b, long long nb,
+                  long long pb, int is_xyz, unsigned char* scratch, int sm_count, cudaStream_t st,
+                  Prepared* A, Prepared* B);
 unsigned long long per_item_bound(const Variant* v);
 Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
                      int is_auto, long long item_begin, unsigned long long* counts,
