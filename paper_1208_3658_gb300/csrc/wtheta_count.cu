@@ -406,12 +406,12 @@ __global__ void __launch_bounds__(64) k_joint_keys(const double* __restrict__ a,
 
 // FP32 and FP64 copies of both catalogues in the joint order (order: the
 // sorted positions of x, a's points first): a's at [0, na) with sentinels up
-// to pa, b's at [pa, pa + nb) with sentinels up to pa + pb (tags 0 and 1); the
-// FP64 copy has stride pa + pb, and each FP32 point keeps in w its index
-// within its own catalogue.
+// to pa, b's at [pa, pa + nb) with sentinels up to pa + pb (tags tag0 and
+// tag0 + 1); the FP64 copy has stride pa + pb, and each FP32 point keeps in w
+// its index within its own catalogue.
 __global__ void k_gather_joint(const double* __restrict__ x, long long na, long long pa,
                                long long nb, long long pb, const unsigned* __restrict__ order,
-                               float4* __restrict__ p32, double* __restrict__ s64) {
+                               int tag0, float4* __restrict__ p32, double* __restrict__ s64) {
     const long long N = na + nb, P = pa + pb;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P;
          i += (long long)gridDim.x * blockDim.x) {
@@ -426,7 +426,7 @@ __global__ void k_gather_joint(const double* __restrict__ x, long long na, long 
             pz = x[2 * N + k];
             q = point32(px, py, pz, in_b ? k - na : k);
         } else {
-            q = sentinel32(in_b ? 1 : 0, j - n);
+            q = sentinel32(tag0 + (in_b ? 1 : 0), j - n);
             px = q.x;
             py = q.y;
             pz = q.z;
@@ -1459,18 +1459,79 @@ __device__ __forceinline__ void warp_stat(unsigned a, bool flag, unsigned w) {
                      : "memory");
 }
 
+// One round of jobs of kind T: this lane's share of job `run` (active: the
+// lane has one; steps t0, t0 + ts, ... of the job, its ts lanes adjacent and
+// ts a power of two).  Span jobs are settled by the first lane of each job
+// from the counts summed over its ts lanes; the return value is the job (bit
+// 30 set) if it has to go pair by pair, else 0.
+template <int NT, int R, int JU, int HM, bool ST>
+__device__ __forceinline__ unsigned job_round(int T, unsigned run, bool active, int t0, int ts,
+                                              unsigned sIJ, unsigned bxy, unsigned bz,
+                                              unsigned lut, unsigned band, unsigned sC,
+                                              unsigned col, const PairParams& p,
+                                              const Segment& S, bool stats, unsigned stat) {
+    constexpr unsigned NP = (unsigned)(R * kChunk);
+    const int lane = threadIdx.x & 31;
+    unsigned n_recheck = 0, fb = 0;
+    bool settled = false;
+    if (T == kJobExact) {
+        if (active) exact_job<NT, R, JU, HM>(run, t0, ts, sIJ, bxy, bz, lut, sC, col, p, S, n_recheck);
+    } else {
+        unsigned neg1 = 0, neg2 = 0;
+        float mb1 = __int_as_float(0x7f800000), mb2 = mb1;
+        if (active)
+            span_part<NT, R, JU, HM>(T, run, t0 * JU, ts * JU, sIJ, bxy, bz, band, S, neg1, neg2,
+                                     mb1, mb2);
+#pragma unroll 1
+        for (int o = ts >> 1; o > 0; o >>= 1) {
+            neg1 += __shfl_xor_sync(0xffffffffu, neg1, o);
+            neg2 += __shfl_xor_sync(0xffffffffu, neg2, o);
+            mb1 = fminf(mb1, __shfl_xor_sync(0xffffffffu, mb1, o));
+            mb2 = fminf(mb2, __shfl_xor_sync(0xffffffffu, mb2, o));
+        }
+        if (active && t0 == 0) {
+            settled = span_settle<NT, R, JU, HM>(T, run, band, col, neg1, neg2, mb1, mb2);
+            if (!settled) fb = run | (1u << 30);
+        }
+    }
+    if (ST && stats) {
+        warp_stat(stat + 8u, settled, NP);
+        if (__any_sync(0xffffffffu, n_recheck != 0)) {
+            unsigned long long v = n_recheck;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0)
+                asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(stat), "l"(v) : "memory");
+        }
+    }
+    return fb;
+}
+
+// Lanes per job for a round of m < 32 jobs: the largest power of two with
+// m ts <= 32 (span jobs: at most the chunk's steps, kChunk / JU).
+template <int JU>
+__device__ __forceinline__ int round_share(int T, int m) {
+    int ts = 1 << (31 - __clz(32 / m));
+    if (T != kJobExact) ts = min(ts, kChunk / JU);
+    return ts;
+}
+
 // A warp's share of one item with span binning: units of its own sub-tile
 // first, then those left of the others (shared counters at address units, one
 // per sub-tile).  Each lane classifies its group against every chunk of a
 // unit; a chunk in one slot is counted at once, the others become jobs (the
-// warp's rings at shared address ring, 32 words per kind).  At the end the
-// warp runs what is left in its rings, then the diagonal units of an auto
-// count it took (pair by pair, with the i < j mask).  The tile pair (I, J)
-// stays in shared memory (sIJ) and the statistics go to the block's shared
-// counters (stat: rechecks, span pairs, skipped pairs), so that the rounds
-// run with few live registers.
+// warp's rings in the block's ring array at shared address rings, 32 words
+// per kind) and a ring that fills runs as one round.  When every unit is
+// taken, the jobs left in all the warps' rings are pooled and shared out
+// evenly (a warp would otherwise run its own leftovers in partial rounds
+// while the others wait at the next item's barrier); then the diagonal units
+// of an auto count that the warp took go pair by pair, with the i < j mask.
+// The tile pair (I, J) stays in shared memory (sIJ) and the statistics go to
+// the block's shared counters (stat: rechecks, span pairs, skipped pairs), so
+// that the rounds run with few live registers.  Every thread of the block
+// calls this once per item (it holds block barriers).
 template <int NT, int R, int JU, int HM, bool ST>
-__device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigned sIJ,
+__device__ __forceinline__ void span_item(unsigned units, unsigned rings, unsigned sIJ,
                                           unsigned bxy, unsigned bz, unsigned lut, unsigned caps,
                                           unsigned band, unsigned sC, unsigned hist,
                                           const PairParams& p, const Segment& S, bool diag,
@@ -1480,10 +1541,12 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
     constexpr int NW = NT / 32, SA = 32 * R, UPS = 4, UB = TB / UPS, CPU = UB / kChunk;
     constexpr unsigned row_bytes = PK::ROWB;
     constexpr unsigned NP = (unsigned)(R * kChunk);
+    constexpr unsigned RING_BYTES = 4u * kJobKinds * 32u;  // one warp's rings
     static_assert(NW <= 8 && TB / kChunk <= 256 && UB % kChunk == 0 && kChunk % JU == 0 &&
                       NW * UPS <= 32,
                   "job fields");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned ring = rings + RING_BYTES * (unsigned)warp;
     const unsigned col = hist + 4u * (unsigned)(HM == kHistWarpRed ? warp : tid);
     const bool stats = ST && p.stats != nullptr;
     unsigned fills = 0;      // jobs waiting per kind, 8 bits each
@@ -1516,10 +1579,10 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
             }
             cn = ub / kChunk;
         }
-        const bool done = k == NW;
+        if (k == NW) break;  // every unit taken: the leftovers are pooled below
         // the chunk's job word with its kind + 1 in bits 30-31 (0: none)
         unsigned kj = 0;
-        if (!done) {
+        {
             const int c = cn;
             cn = (c + 1) % CPU == 0 ? -1 : c + 1;
             const uint4 gbu = lds_u4(caps + 16u * (unsigned)c);
@@ -1543,7 +1606,7 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
         }
         // Most chunks fill no ring: their jobs are appended at once and the
         // warp takes the next chunk (fills stay below 64, so 8 bits each).
-        if (!done) {
+        {
             const unsigned kind = kj >> 30;
             const unsigned m1 = __ballot_sync(0xffffffffu, kind == 1u);
             const unsigned m2 = __ballot_sync(0xffffffffu, kind == 2u);
@@ -1562,10 +1625,10 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
                 continue;
             }
         }
-        // Ring steps: the two-slot ring, the pair-by-pair ring for the
-        // two-slot jobs that found a value near their edge, the three-slot
-        // ring, the same for its jobs, then the pair-by-pair ring for the
-        // chunk's own job.  One code path per kind of round.
+        // A ring that fills runs as one round, one job per lane: the two-slot
+        // ring, the pair-by-pair ring for the two-slot jobs that found a value
+        // near their edge, the three-slot ring, the same for its jobs, then the
+        // pair-by-pair ring for the chunk's own job.  One code path per kind.
         unsigned fb = 0;  // this lane's job that has to go pair by pair (bit 30: valid)
 #pragma unroll 1
         for (int st = 0; st < 5; ++st) {
@@ -1574,70 +1637,83 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned ring, unsigne
             const unsigned word = from_fb ? fb : kj;
             const bool push = from_fb ? fb != 0u : (kj >> 30) == (unsigned)(T + 1);
             if (from_fb) fb = 0u;
-            const bool flush = done && (T != kJobExact || st == 4);
             const unsigned m = __ballot_sync(0xffffffffu, push);
             const int fill = (int)((fills >> (8 * T)) & 255u);
             const int n = __popc(m);
-            if (n == 0 && !(flush && fill > 0)) continue;
+            if (n == 0) continue;
             const unsigned rt = ring + 128u * (unsigned)T;
             const int pos = fill + __popc(m & ((1u << lane) - 1u));
             const unsigned job = word & 0x3FFFFFFFu;
             if (push && pos < 32) sts_u32(rt + 4u * (unsigned)pos, job);
             const int total = fill + n;
-            if (total < 32 && !flush) {
+            if (total < 32) {
                 fills += (unsigned)n << (8 * T);
                 continue;
             }
-            // A full round gives each lane a job.  The last, partial round of
-            // a ring shares each job among ts lanes (ts a power of two), lane
-            // q % ts taking the job's steps q % ts, q % ts + ts, ...
-            int ts = 1;
-            if (total < 32)
-                ts = 1 << (31 - __clz(32 / total));
-            if (T != kJobExact) ts = min(ts, kChunk / JU);
-            const int jl = lane / ts, t0 = lane % ts;
             __syncwarp();
-            const unsigned run = lds_u32(rt + 4u * (unsigned)min(jl, 31));
+            const unsigned run = lds_u32(rt + 4u * (unsigned)lane);
             __syncwarp();
             if (push && pos >= 32) sts_u32(rt + 4u * (unsigned)(pos - 32), job);
-            fills = (fills & ~(255u << (8 * T))) | ((unsigned)max(total - 32, 0) << (8 * T));
-            const bool active = jl < total;
-            unsigned n_recheck = 0;
-            bool settled = false;
-            if (T == kJobExact) {
-                if (active)
-                    exact_job<NT, R, JU, HM>(run, t0, ts, sIJ, bxy, bz, lut, sC, col, p, S,
-                                             n_recheck);
-            } else {
-                unsigned neg1 = 0, neg2 = 0;
-                float mb1 = __int_as_float(0x7f800000), mb2 = mb1;
-                if (active)
-                    span_part<NT, R, JU, HM>(T, run, t0 * JU, ts * JU, sIJ, bxy, bz, band, S,
-                                             neg1, neg2, mb1, mb2);
-#pragma unroll 1
-                for (int o = ts >> 1; o > 0; o >>= 1) {
-                    neg1 += __shfl_xor_sync(0xffffffffu, neg1, o);
-                    neg2 += __shfl_xor_sync(0xffffffffu, neg2, o);
-                    mb1 = fminf(mb1, __shfl_xor_sync(0xffffffffu, mb1, o));
-                    mb2 = fminf(mb2, __shfl_xor_sync(0xffffffffu, mb2, o));
-                }
-                if (active && t0 == 0) {
-                    settled = span_settle<NT, R, JU, HM>(T, run, band, col, neg1, neg2, mb1, mb2);
-                    if (!settled) fb = run | (1u << 30);
-                }
-            }
-            if (stats) {
-                warp_stat(stat + 8u, settled, NP);
-                if (__any_sync(0xffffffffu, n_recheck != 0)) {
-                    unsigned long long v = n_recheck;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0)
-                        asm volatile("red.shared.add.u64 [%0], %1;" ::"r"(stat), "l"(v) : "memory");
-                }
-            }
+            fills = (fills & ~(255u << (8 * T))) | ((unsigned)(total - 32) << (8 * T));
+            fb = job_round<NT, R, JU, HM, ST>(T, run, true, 0, 1, sIJ, bxy, bz, lut, band, sC, col,
+                                              p, S, stats, stat);
         }
-        if (done) break;
+    }
+    // The leftovers of every warp, pooled.  Once all warps are here the rings
+    // are quiescent; each warp publishes its fills in its unit counter (no
+    // longer claimed), and the jobs of each kind, the rings taken in warp
+    // order, are shared out in contiguous slices of about n / NW jobs, each
+    // slice one round with the lanes of a job adjacent.
+    __syncthreads();
+    if (lane == 0) sts_u32(units + 4u * (unsigned)warp, fills);
+    __syncthreads();
+    unsigned fl[NW];
+#pragma unroll
+    for (int q = 0; q < NW; ++q) fl[q] = lds_u32(units + 4u * (unsigned)q);
+    unsigned fb0 = 0, fb1 = 0;  // pooled two- and three-slot jobs to redo pair by pair
+#pragma unroll 1
+    for (int T = 0; T < kJobKinds; ++T) {
+        int n = 0;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) n += (int)((fl[q] >> (8 * T)) & 255u);
+        const int lo = warp * n / NW, m = (warp + 1) * n / NW - lo;
+        if (m == 0) continue;
+        const int ts = round_share<JU>(T, m);
+        const int jl = lane / ts;
+        // job lo + jl of the pool: position i of warp q's ring
+        int i = lo + min(jl, m - 1), q = 0;
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) {
+            const int f = (int)((fl[w] >> (8 * T)) & 255u);
+            const bool past = q == w && i >= f;
+            i -= past ? f : 0;
+            q += past ? 1 : 0;
+        }
+        const unsigned run =
+            lds_u32(rings + RING_BYTES * (unsigned)q + 128u * (unsigned)T + 4u * (unsigned)i);
+        const unsigned fb = job_round<NT, R, JU, HM, ST>(T, run, jl < m, lane % ts, ts, sIJ, bxy, bz,
+                                                         lut, band, sC, col, p, S, stats, stat);
+        if (T == kJobTwo) fb0 = fb;
+        if (T == kJobThree) fb1 = fb;
+    }
+    __syncthreads();  // every pooled job read: the rings are free again
+    // pooled span jobs that found a value near an edge (rare): pair by pair,
+    // each warp its own, through its pair-by-pair ring
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+        const unsigned fb = h == 0 ? fb0 : fb1;
+        const unsigned m = __ballot_sync(0xffffffffu, fb != 0u);
+        if (m == 0u) continue;
+        const int n = __popc(m);
+        const unsigned rt = ring + 128u * (unsigned)kJobExact;
+        if (fb) sts_u32(rt + 4u * (unsigned)__popc(m & ((1u << lane) - 1u)), fb & 0x3FFFFFFFu);
+        __syncwarp();
+        const int ts = round_share<JU>(kJobExact, n);
+        const int jl = lane / ts;
+        const unsigned run = lds_u32(rt + 4u * (unsigned)min(jl, n - 1));
+        __syncwarp();
+        job_round<NT, R, JU, HM, ST>(kJobExact, run, jl < n, lane % ts, ts, sIJ, bxy, bz, lut, band,
+                                     sC, col, p, S, stats, stat);
     }
     // the diagonal units taken: pair by pair, i < j
 #pragma unroll 1
@@ -1776,8 +1852,7 @@ __global__ void __launch_bounds__(NT, R == 8 ? 640 / NT : 1) k_pairs(const __gri
         if constexpr (!DEF && HM != kHistWarp) spans = p.span && S.b_caps;
         if constexpr (!DEF && HM != kHistWarp) {
             if (spans)
-                span_item<NT, R, JU, HM, ST>(smem_addr(s_units),
-                                         smem_addr(s_ring + warp * (kJobKinds * 32)),
+                span_item<NT, R, JU, HM, ST>(smem_addr(s_units), smem_addr(s_ring),
                                          smem_addr(s_IJ[n_items & 1]), a_bxy, a_bz, a_lut, a_cap, a_band, a_c,
                                          a_hist, p, S, diag, smem_addr(s_stat));
         }
@@ -2161,8 +2236,8 @@ size_t prepare_joint_bytes(long long na, long long pa, long long nb, long long p
 }
 
 int prepare_joint(const double* a, long long na, long long pa, const double* b, long long nb,
-                  long long pb, int is_xyz, unsigned char* scratch, int sm_count, cudaStream_t st,
-                  Prepared* A, Prepared* B) {
+                  long long pb, int is_xyz, int tag0, unsigned char* scratch, int sm_count,
+                  cudaStream_t st, Prepared* A, Prepared* B) {
     TraceRange trace("prepare");
     const long long N = na + nb, P = pa + pb;
     if (N >= (1LL << 32) - 1) return WTHETA_EINVAL;  // 32-bit positions in the sort
@@ -2183,8 +2258,8 @@ int prepare_joint(const double* a, long long na, long long pa, const double* b, 
         key_passes(S, N, st);
     }
     if (P > 0) {
-        k_gather_joint<<<launch_grid(P, sm_count), 256, 0, st>>>(x, na, pa, nb, pb, S.idx[0], p32,
-                                                                 s64);
+        k_gather_joint<<<launch_grid(P, sm_count), 256, 0, st>>>(x, na, pa, nb, pb, S.idx[0], tag0,
+                                                                 p32, s64);
         k_chunk_caps<<<launch_grid(P, sm_count), 256, 0, st>>>(p32, P, P, c32);
         count_launch(2);
     }
@@ -2369,7 +2444,7 @@ static int count_impl(const double* ca, long long n_a, const double* cb, long lo
     unsigned long long* cursor = (unsigned long long*)sp;
     Prepared A, B;
     rc = prepare_joint(ca, n_a, pa, is_auto ? nullptr : cb, is_auto ? 0 : n_b, is_auto ? 0 : pb,
-                       is_xyz, sp + 256, di.sm_count, st, &A, &B);
+                       is_xyz, 0, sp + 256, di.sm_count, st, &A, &B);
     if (is_auto) B = A;
     if (!rc) rc = check_cuda(cudaMemsetAsync(cursor, 0, 2 * sizeof(unsigned long long), st));
 
@@ -2514,7 +2589,7 @@ static int count_wtheta_impl(const double* cd, long long nd, const double* cr, l
     unsigned long long* d_kept = (unsigned long long*)(m + 256 + 2048);
     static_assert(3 * sizeof(Segment) <= 1024 && 3 * sizeof(CullSeg) <= 1024, "tables fit");
     Prepared D, R;
-    rc = prepare_joint(cd, nd, pd, cr, nr, pr, is_xyz, m + off_prep, di.sm_count, st, &D, &R);
+    rc = prepare_joint(cd, nd, pd, cr, nr, pr, is_xyz, 0, m + off_prep, di.sm_count, st, &D, &R);
     TileCap* caps_d = (TileCap*)(m + off_caps);
     TileCap* caps_r = caps_d + td;  // R's tiles follow D's in the joint copies
     if (!rc && (cull || n_shards > 1) && td + tr > 0)

@@ -141,12 +141,15 @@ int prepare(const double* coords, long long n, long long n_pad, int is_xyz, int 
 // The one or two catalogues of a count prepared together (b absent: nb = pb
 // = 0): one conversion and key launch, one sort of the na + nb points, one
 // gather into FP32 and FP64 copies with a's points at [0, pa) and b's at
-// [pa, pa + pb) (each catalogue tile-padded with sentinels), one launch for
-// the chunk spheres of both.  scratch: prepare_joint_bytes(na, pa, nb, pb).
+// [pa, pa + pb) (each catalogue tile-padded with sentinels of tags tag0 and
+// tag0 + 1: catalogues that a count may pair need different tags), one
+// launch for the chunk spheres of both.  scratch: prepare_joint_bytes(na, pa,
+// nb, pb); a and b may lie in its first 16 (na + nb) bytes (the FP32 copies,
+// written after both are read).
 size_t prepare_joint_bytes(long long na, long long pa, long long nb, long long pb);
 int prepare_joint(const double* a, long long na, long long pa, const double* b, long long nb,
-                  long long pb, int is_xyz, unsigned char* scratch, int sm_count, cudaStream_t st,
-                  Prepared* A, Prepared* B);
+                  long long pb, int is_xyz, int tag0, unsigned char* scratch, int sm_count,
+                  cudaStream_t st, Prepared* A, Prepared* B);
 unsigned long long per_item_bound(const Variant* v);
 Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
                      int is_auto, long long item_begin, unsigned long long* counts,

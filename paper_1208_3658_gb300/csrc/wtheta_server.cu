@@ -133,8 +133,9 @@ size_t cull_bytes(const wtheta_server* S, const Request* r) {
     if (!r->cull) return 0;
     const long long T = (long long)S->v->nt * S->v->r;
     size_t b = 256;                                    // kept counters
-    for (int c = 0; c < r->ncat; ++c)
-        b += ((size_t)(round_up(r->n[c], T) / T) * sizeof(TileCap) + 255) / 256 * 256;
+    for (int c = 0; c + 1 < r->ncat; c += 2)           // caps of each prepared pair
+        b += ((size_t)(round_up(r->n[c], T) / T + round_up(r->n[c + 1], T) / T) * sizeof(TileCap) +
+              255) / 256 * 256;
     for (int k = 0; k < r->ncount; ++k) b += ((size_t)count_items(r, T, k) * 4 + 255) / 256 * 256;
     return b;
 }
@@ -142,8 +143,9 @@ size_t cull_bytes(const wtheta_server* S, const Request* r) {
 size_t request_bytes(const wtheta_server* S, const Request* r) {
     const long long T = (long long)S->v->nt * S->v->r;
     size_t b = 0;
-    for (int c = 0; c < r->ncat; ++c)
-        b += (prepare_bytes(r->n[c], round_up(r->n[c], T), 0) + 255) / 256 * 256;
+    for (int c = 0; c + 1 < r->ncat; c += 2)
+        b += (prepare_joint_bytes(r->n[c], round_up(r->n[c], T), r->n[c + 1],
+                                  round_up(r->n[c + 1], T)) + 255) / 256 * 256;
     b += (size_t)r->ncount * (S->K + 2) * 8 + 256;    // counts
     b += sizeof(Segment) * 4 + 256;                    // the request's segment table
     b += cull_bytes(S, r);                             // caps and kept tile pairs
@@ -177,20 +179,27 @@ int admit(wtheta_server* S, Request* r) {
     p += ((size_t)r->ncount * (S->K + 2) * 8 + 255) / 256 * 256;
     r->d_segs = (Segment*)p;
     p += (sizeof(Segment) * 4 + 255) / 256 * 256;
-    for (int c = 0; c < r->ncat && !rc; ++c) {
-        const long long np = round_up(r->n[c], T);
-        const size_t pb = (prepare_bytes(r->n[c], np, 0) + 255) / 256 * 256;
-        // The raw RA/Dec (16 B/pt) is uploaded into the start of the region,
-        // where the FP32 copies (16 B/pt, tile-padded) will go: the conversion
-        // reads it into the FP64 area before, in stream order, the spatial
-        // scatter overwrites it with the FP32 copies.
+    // The catalogues are prepared two by two, (D, R) of an auto request and
+    // (D1, R1), (D2, R2) of a cross one, each pair by one pipeline (sentinel
+    // tags 0-1 and 2-3, so that no count pairs two coinciding sentinels).
+    for (int c = 0; c + 1 < r->ncat && !rc; c += 2) {
+        const long long na = r->n[c], nb = r->n[c + 1];
+        const long long pa = round_up(na, T), pb = round_up(nb, T);
+        const size_t bytes = (prepare_joint_bytes(na, pa, nb, pb) + 255) / 256 * 256;
+        // The raw RA/Dec of both (16 B/pt) is uploaded into the start of the
+        // region, where the FP32 copies (16 B/pt, tile-padded) will go: the
+        // conversion reads it before, in stream order, the gather overwrites it.
         unsigned char* region = p;
-        p += pb;
-        rc = check_cuda(cudaMemcpyAsync(region, r->host_in[c], (size_t)r->n[c] * 16,
+        p += bytes;
+        rc = check_cuda(cudaMemcpyAsync(region, r->host_in[c], (size_t)na * 16,
                                         cudaMemcpyHostToDevice, S->up));
+        if (!rc)
+            rc = check_cuda(cudaMemcpyAsync(region + (size_t)na * 16, r->host_in[c + 1],
+                                            (size_t)nb * 16, cudaMemcpyHostToDevice, S->up));
         if (rc) break;
-        rc = prepare((const double*)region, r->n[c], np, 0, c, region,
-                     S->sm_count, S->up, &r->prep[c]);
+        rc = prepare_joint((const double*)region, na, pa, (const double*)(region + (size_t)na * 16),
+                           nb, pb, 0, c, region, S->sm_count, S->up, &r->prep[c],
+                           &r->prep[c + 1]);
     }
     if (!rc) rc = check_cuda(cudaMemsetAsync(r->d_counts, 0, (size_t)r->ncount * (S->K + 2) * 8, S->up));
     if (rc) return rc;
@@ -223,11 +232,15 @@ int admit(wtheta_server* S, Request* r) {
         r->d_kept = (unsigned long long*)p;
         p += 256;
         TileCap* caps[4] = {nullptr, nullptr, nullptr, nullptr};
-        for (int c = 0; c < r->ncat && !rc; ++c) {
+        for (int c = 0; c + 1 < r->ncat && !rc; c += 2) {
+            // one launch over a prepared pair: the second's tiles follow the first's
+            const long long ta = round_up(r->n[c], T) / T, tb = round_up(r->n[c + 1], T) / T;
             caps[c] = (TileCap*)p;
-            const long long tiles = round_up(r->n[c], T) / T;
-            p += ((size_t)tiles * sizeof(TileCap) + 255) / 256 * 256;
-            rc = launch_tile_caps(r->prep[c].p32, r->n[c], (int)T, tiles, caps[c], S->up);
+            caps[c + 1] = caps[c] + ta;
+            p += ((size_t)(ta + tb) * sizeof(TileCap) + 255) / 256 * 256;
+            if (ta + tb > 0)
+                rc = launch_tile_caps(r->prep[c].p32, (ta + tb) * T, (int)T, ta + tb, caps[c],
+                                      S->up);
         }
         if (!rc) rc = check_cuda(cudaMemsetAsync(r->d_kept, 0, 4 * 8, S->up));
         static const int auto_a[3] = {0, 0, 1}, auto_b[3] = {0, 1, 1};
