@@ -2322,16 +2322,19 @@ int launch_cull_batch(const CullSeg* cs, int n_segs, long long total, double the
 }
 
 unsigned long long per_item_bound(const Variant* v) {
-    // A thread bins R x TB pairs per unit of its own sub-tile and may take
-    // the units of every other sub-tile of the item (NT/32 of them): NT/32 x
-    // R TB pairs of its own groups.  With span jobs it also runs at most one
-    // job (R x 32 pairs) per round of its warp: as many pairs again, plus one
-    // last partial round per kind of job.  A per-warp column gains 32 times
-    // as much.
+    // A thread bins (or settles by chunk) R x TB pairs per unit of its own
+    // sub-tile and may take the units of every other sub-tile of the item
+    // (NT/32 of them): own = NT/32 x R TB pairs of its own groups.  With span
+    // jobs it also runs at most one job (R x 32 pairs) per round of its warp;
+    // the warp's jobs are at most one per lane and chunk, plus one
+    // pair-by-pair job for each span job that found a value near an edge, so
+    // its full rounds add at most 2 own; after them come at most three pooled
+    // rounds and two rounds of pooled jobs redone pair by pair.  A per-warp
+    // column gains 32 times as much.
     const unsigned long long own = (unsigned long long)(v->nt / 32) * (unsigned long long)v->r *
                                    (unsigned long long)v->nt * (unsigned long long)v->r;
     return (v->hm == kHistWarp || v->hm == kHistWarpRed ? 32ull : 1ull) *
-           (2ull * own + 3ull * 32ull * (unsigned)v->r);
+           (3ull * own + 5ull * 32ull * (unsigned)v->r);
 }
 
 Segment make_segment(const Prepared& A, const Prepared& B, long long ta, long long tb,
