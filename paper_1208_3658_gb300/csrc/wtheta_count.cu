@@ -938,16 +938,25 @@ __device__ __forceinline__ bool bin_values(const float (&s)[NV], unsigned col, u
     return any_band;
 }
 
+// A step's NV squared chords, passed by value.
+template <int NV>
+struct StepValues {
+    float v[NV];
+};
+
 // Rare: the step held values inside a guard band.  Given the step's values
 // again, take back their provisional counts and add each to the row its FP64
-// recheck gives (one copy of the recheck code, in a loop over a bitmask).
-template <int NT, int R, int NV, int HM, typename Cnt>
-__device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsigned col, unsigned lut,
-                                                 int shift, int base, int top_idx,
-                                                 unsigned row_bytes, int K, const Segment& S,
-                                                 long long a0, long long bj,
-                                                 unsigned sC,
-                                                 Cnt& n_recheck) {
+// recheck gives (one copy of the recheck code, in a loop over a bitmask);
+// returns the number of values rechecked.  Kept out of line: its FP64
+// registers then do not weigh on the loops that call it.
+template <int NT, int R, int NV, int HM>
+__device__ __noinline__ unsigned recount_band_values(const StepValues<NV> sv, unsigned col,
+                                                     unsigned lut, int shift, int base,
+                                                     int top_idx, unsigned row_bytes, int K,
+                                                     const Segment& S, long long a0, long long bj,
+                                                     unsigned sC) {
+    const float (&s)[NV] = sv.v;
+    unsigned n_recheck = 0;
     unsigned mask = 0;
     int hint_v = -1, hint = -1;  // the first such value and its edge's lower slot
 #pragma unroll
@@ -971,6 +980,7 @@ __device__ __forceinline__ void recount_band_values(const float (&s)[NV], unsign
         ++n_recheck;
         hist_add<HM>(col + slot * row_bytes, 1u);
     }
+    return n_recheck;
 }
 
 // Squared chords of JU consecutive B points (from j) with the thread's R A
@@ -1033,10 +1043,10 @@ __device__ __forceinline__ void exact_steps(int j0, int j1, unsigned bxy, unsign
         const float m = min_of(s);
         if (!(m <= hf)) continue;
         if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx)) {
-            float s2[NV];
-            chords<NT, R, JU, DIAG>(s2, bxy, bz, ax, ay, az, j, a_first);
-            recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, row_bytes, K,
-                                               S, a0, b0 + j, sC, n_recheck);
+            StepValues<NV> s2;
+            chords<NT, R, JU, DIAG>(s2.v, bxy, bz, ax, ay, az, j, a_first);
+            n_recheck += recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx,
+                                                            row_bytes, K, S, a0, b0 + j, sC);
         }
     }
 }
@@ -1212,11 +1222,12 @@ __device__ __forceinline__ void tile_pass(unsigned bxy, unsigned bz, unsigned lu
                 const int st = __ffs(mask) - 1;
                 mask &= mask - 1;
                 const int j = jb + st * JU;
-                float s[NV];
-                chords<NT, R, JU, DIAG>(s, bxy, bz, ax, ay, az, j, a_first);
-                if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx))
-                    recount_band_values<NT, R, NV, HM>(s, col, lut, shift, base, top_idx,
-                                                       row_bytes, K, S, a0, b0 + j, sC, n_recheck);
+                StepValues<NV> s;
+                chords<NT, R, JU, DIAG>(s.v, bxy, bz, ax, ay, az, j, a_first);
+                if (bin_values<NV, HM>(s.v, col, lut, shift, base, top_idx))
+                    n_recheck += recount_band_values<NT, R, NV, HM>(s, col, lut, shift, base,
+                                                                    top_idx, row_bytes, K, S, a0,
+                                                                    b0 + j, sC);
             }
         }
         return;
@@ -1330,12 +1341,12 @@ __device__ __forceinline__ void exact_chunk(int c0, int rot, int t0, int ts, int
         chords<NT, R, 1, false>(s, bxy, bz, ax, ay, az, j, 0);
         if (!(min_of(s) <= hf)) continue;
         if (bin_values<NV, HM>(s, col, lut, shift, base, top_idx)) {
-            float s2[NV];
-            chords<NT, R, 1, false>(s2, bxy, bz, ax, ay, az, j, 0);
+            StepValues<NV> s2;
+            chords<NT, R, 1, false>(s2.v, bxy, bz, ax, ay, az, j, 0);
             const long long a0 = lds_s64(sIJ) * TA + a_first;
             const long long b0 = lds_s64(sIJ + 8u) * TB;
-            recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx, PK::ROWB,
-                                               p.tab.K, S, a0, b0 + j, sC, n_recheck);
+            n_recheck += recount_band_values<NT, R, NV, HM>(s2, col, lut, shift, base, top_idx,
+                                                            PK::ROWB, p.tab.K, S, a0, b0 + j, sC);
         }
     }
 }
