@@ -1564,6 +1564,11 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned rings, unsign
     unsigned diag_units = 0;  // diagonal units taken (bit sub UPS + u)
     int k = 0, cap_sub = -1, cn = -1;  // cn: next chunk of the current unit, -1: none
     float4 ga = make_float4(0.f, 0.f, 0.f, 0.f);
+    // A block of one warp has nobody to pool its leftovers with: when its
+    // units are all taken it flushes its own rings in the ring steps below
+    // (partial rounds, each job shared among lanes), so that the span jobs
+    // redone pair by pair join the pair-by-pair ring's last round.
+    bool done = false;
 #pragma unroll 1
     for (;;) {
 #pragma unroll 1
@@ -1590,10 +1595,13 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned rings, unsign
             }
             cn = ub / kChunk;
         }
-        if (k == NW) break;  // every unit taken: the leftovers are pooled below
+        if (k == NW) {
+            if constexpr (NW > 1) break;  // every unit taken: the leftovers are pooled below
+            done = true;
+        }
         // the chunk's job word with its kind + 1 in bits 30-31 (0: none)
         unsigned kj = 0;
-        {
+        if (!done) {
             const int c = cn;
             cn = (c + 1) % CPU == 0 ? -1 : c + 1;
             const uint4 gbu = lds_u4(caps + 16u * (unsigned)c);
@@ -1617,7 +1625,7 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned rings, unsign
         }
         // Most chunks fill no ring: their jobs are appended at once and the
         // warp takes the next chunk (fills stay below 64, so 8 bits each).
-        {
+        if (!done) {
             const unsigned kind = kj >> 30;
             const unsigned m1 = __ballot_sync(0xffffffffu, kind == 1u);
             const unsigned m2 = __ballot_sync(0xffffffffu, kind == 2u);
@@ -1648,83 +1656,95 @@ __device__ __forceinline__ void span_item(unsigned units, unsigned rings, unsign
             const unsigned word = from_fb ? fb : kj;
             const bool push = from_fb ? fb != 0u : (kj >> 30) == (unsigned)(T + 1);
             if (from_fb) fb = 0u;
+            // one-warp blocks, units all taken: every ring but the
+            // pair-by-pair one flushes at its step, that one at the last
+            const bool flush = done && (T != kJobExact || st == 4);
             const unsigned m = __ballot_sync(0xffffffffu, push);
             const int fill = (int)((fills >> (8 * T)) & 255u);
             const int n = __popc(m);
-            if (n == 0) continue;
+            if (n == 0 && !(flush && fill > 0)) continue;
             const unsigned rt = ring + 128u * (unsigned)T;
             const int pos = fill + __popc(m & ((1u << lane) - 1u));
             const unsigned job = word & 0x3FFFFFFFu;
             if (push && pos < 32) sts_u32(rt + 4u * (unsigned)pos, job);
             const int total = fill + n;
-            if (total < 32) {
+            if (total < 32 && !flush) {
                 fills += (unsigned)n << (8 * T);
                 continue;
             }
+            // a full round gives each lane a job; a flushed partial round
+            // shares each job among ts lanes (round_share)
+            const int ts = total < 32 ? round_share<JU>(T, total) : 1;
+            const int jl = lane / ts;
             __syncwarp();
-            const unsigned run = lds_u32(rt + 4u * (unsigned)lane);
+            const unsigned run = lds_u32(rt + 4u * (unsigned)min(jl, 31));
             __syncwarp();
             if (push && pos >= 32) sts_u32(rt + 4u * (unsigned)(pos - 32), job);
-            fills = (fills & ~(255u << (8 * T))) | ((unsigned)(total - 32) << (8 * T));
-            fb = job_round<NT, R, JU, HM, ST>(T, run, true, 0, 1, sIJ, bxy, bz, lut, band, sC, col,
-                                              p, S, stats, stat);
+            fills = (fills & ~(255u << (8 * T))) | ((unsigned)max(total - 32, 0) << (8 * T));
+            fb = job_round<NT, R, JU, HM, ST>(T, run, jl < total, lane % ts, ts, sIJ, bxy, bz, lut,
+                                              band, sC, col, p, S, stats, stat);
         }
+        if (done) break;
     }
-    // The leftovers of every warp, pooled.  Once all warps are here the rings
-    // are quiescent; each warp publishes its fills in its unit counter (no
-    // longer claimed), and the jobs of each kind, the rings taken in warp
-    // order, are shared out in contiguous slices of about n / NW jobs, each
-    // slice one round with the lanes of a job adjacent.
-    __syncthreads();
-    if (lane == 0) sts_u32(units + 4u * (unsigned)warp, fills);
-    __syncthreads();
-    unsigned fl[NW];
+    // The leftovers of every warp, pooled (blocks of several warps).  Once
+    // all warps are here the rings are quiescent; each warp publishes its
+    // fills in its unit counter (no longer claimed), and the jobs of each
+    // kind, the rings taken in warp order, are shared out in contiguous slices
+    // of about n / NW jobs, each slice one round with the lanes of a job
+    // adjacent.
+    if constexpr (NW > 1) {
+        __syncthreads();
+        if (lane == 0) sts_u32(units + 4u * (unsigned)warp, fills);
+        __syncthreads();
+        unsigned fl[NW];
 #pragma unroll
-    for (int q = 0; q < NW; ++q) fl[q] = lds_u32(units + 4u * (unsigned)q);
-    unsigned fb0 = 0, fb1 = 0;  // pooled two- and three-slot jobs to redo pair by pair
+        for (int q = 0; q < NW; ++q) fl[q] = lds_u32(units + 4u * (unsigned)q);
+        unsigned fb0 = 0, fb1 = 0;  // pooled two- and three-slot jobs to redo pair by pair
 #pragma unroll 1
-    for (int T = 0; T < kJobKinds; ++T) {
-        int n = 0;
+        for (int T = 0; T < kJobKinds; ++T) {
+            int n = 0;
 #pragma unroll
-        for (int q = 0; q < NW; ++q) n += (int)((fl[q] >> (8 * T)) & 255u);
-        const int lo = warp * n / NW, m = (warp + 1) * n / NW - lo;
-        if (m == 0) continue;
-        const int ts = round_share<JU>(T, m);
-        const int jl = lane / ts;
-        // job lo + jl of the pool: position i of warp q's ring
-        int i = lo + min(jl, m - 1), q = 0;
+            for (int q = 0; q < NW; ++q) n += (int)((fl[q] >> (8 * T)) & 255u);
+            const int lo = warp * n / NW, m = (warp + 1) * n / NW - lo;
+            if (m == 0) continue;
+            const int ts = round_share<JU>(T, m);
+            const int jl = lane / ts;
+            // job lo + jl of the pool: position i of warp q's ring
+            int i = lo + min(jl, m - 1), q = 0;
 #pragma unroll
-        for (int w = 0; w < NW - 1; ++w) {
-            const int f = (int)((fl[w] >> (8 * T)) & 255u);
-            const bool past = q == w && i >= f;
-            i -= past ? f : 0;
-            q += past ? 1 : 0;
+            for (int w = 0; w < NW - 1; ++w) {
+                const int f = (int)((fl[w] >> (8 * T)) & 255u);
+                const bool past = q == w && i >= f;
+                i -= past ? f : 0;
+                q += past ? 1 : 0;
+            }
+            const unsigned run =
+                lds_u32(rings + RING_BYTES * (unsigned)q + 128u * (unsigned)T + 4u * (unsigned)i);
+            const unsigned fb = job_round<NT, R, JU, HM, ST>(T, run, jl < m, lane % ts, ts, sIJ,
+                                                             bxy, bz, lut, band, sC, col, p, S,
+                                                             stats, stat);
+            if (T == kJobTwo) fb0 = fb;
+            if (T == kJobThree) fb1 = fb;
         }
-        const unsigned run =
-            lds_u32(rings + RING_BYTES * (unsigned)q + 128u * (unsigned)T + 4u * (unsigned)i);
-        const unsigned fb = job_round<NT, R, JU, HM, ST>(T, run, jl < m, lane % ts, ts, sIJ, bxy, bz,
-                                                         lut, band, sC, col, p, S, stats, stat);
-        if (T == kJobTwo) fb0 = fb;
-        if (T == kJobThree) fb1 = fb;
-    }
-    __syncthreads();  // every pooled job read: the rings are free again
-    // pooled span jobs that found a value near an edge (rare): pair by pair,
-    // each warp its own, through its pair-by-pair ring
+        __syncthreads();  // every pooled job read: the rings are free again
+        // pooled span jobs that found a value near an edge (rare): pair by pair,
+        // each warp its own, through its pair-by-pair ring
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-        const unsigned fb = h == 0 ? fb0 : fb1;
-        const unsigned m = __ballot_sync(0xffffffffu, fb != 0u);
-        if (m == 0u) continue;
-        const int n = __popc(m);
-        const unsigned rt = ring + 128u * (unsigned)kJobExact;
-        if (fb) sts_u32(rt + 4u * (unsigned)__popc(m & ((1u << lane) - 1u)), fb & 0x3FFFFFFFu);
-        __syncwarp();
-        const int ts = round_share<JU>(kJobExact, n);
-        const int jl = lane / ts;
-        const unsigned run = lds_u32(rt + 4u * (unsigned)min(jl, n - 1));
-        __syncwarp();
-        job_round<NT, R, JU, HM, ST>(kJobExact, run, jl < n, lane % ts, ts, sIJ, bxy, bz, lut, band,
-                                     sC, col, p, S, stats, stat);
+        for (int h = 0; h < 2; ++h) {
+            const unsigned fb = h == 0 ? fb0 : fb1;
+            const unsigned m = __ballot_sync(0xffffffffu, fb != 0u);
+            if (m == 0u) continue;
+            const int n = __popc(m);
+            const unsigned rt = ring + 128u * (unsigned)kJobExact;
+            if (fb) sts_u32(rt + 4u * (unsigned)__popc(m & ((1u << lane) - 1u)), fb & 0x3FFFFFFFu);
+            __syncwarp();
+            const int ts = round_share<JU>(kJobExact, n);
+            const int jl = lane / ts;
+            const unsigned run = lds_u32(rt + 4u * (unsigned)min(jl, n - 1));
+            __syncwarp();
+            job_round<NT, R, JU, HM, ST>(kJobExact, run, jl < n, lane % ts, ts, sIJ, bxy, bz, lut,
+                                         band, sC, col, p, S, stats, stat);
+        }
     }
     // the diagonal units taken: pair by pair, i < j
 #pragma unroll 1
