@@ -204,10 +204,35 @@ def _host_u64(a):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
 
 
-def _n_points(t, per_point):
+def _n_points(t, per_point, name="coordinates"):
+    """Points in a coordinate tensor, after checking its layout.  Interleaved
+    RA/Dec (per_point 2) is 1-D [ra0, dec0, ra1, ...] or (n, 2); unit vectors
+    (per_point 3) are SoA, (3, n) or 1-D [x0.., y0.., z0..].  The library
+    reads unit vectors with stride n, so a row-major (n, 3) array would give
+    wrong counts: it is refused, as are data that are not float64 and sizes
+    that are not whole points."""
     if t is None:
         return 0
+    if str(t.dtype) != "torch.float64":
+        raise ValueError("%s must be float64, not %s" % (name, t.dtype))
+    if per_point == 3:
+        ok = t.dim() == 1 or (t.dim() == 2 and t.shape[0] == 3)
+        layout = "SoA unit vectors of shape (3, n) or 1-D [x.., y.., z..]"
+    else:
+        ok = t.dim() == 1 or (t.dim() == 2 and t.shape[1] == 2)
+        layout = "interleaved RA/Dec, 1-D [ra0, dec0, ...] or shape (n, 2)"
+    if not ok or t.numel() % per_point:
+        raise ValueError("%s must be %s, not shape %s" % (name, layout, tuple(t.shape)))
     return t.numel() // per_point
+
+
+def _slots(t, n, name="counts"):
+    """Checks that an output tensor holds at least n 8-byte slots (the library
+    writes n of them)."""
+    if t is None or isinstance(t, int):
+        return
+    if t.numel() < n:
+        raise ValueError("%s must hold at least %d slots, not %d" % (name, n, t.numel()))
 
 
 # ---------------------------------------------------------------------------
@@ -247,8 +272,9 @@ def wtheta_count(ra_dec_a, ra_dec_b, edges_deg, is_auto: bool, counts, stream=No
     """ra_dec_*: CUDA float64 tensors [ra0, dec0, ...] (ra_dec_b None for auto);
     counts: CUDA 8-byte tensor of K+2 slots, overwritten."""
     e, ep = _host_f64(edges_deg)
-    na = _n_points(ra_dec_a, 2) if n_a is None else n_a
-    nb = (na if is_auto else _n_points(ra_dec_b, 2)) if n_b is None else n_b
+    na = _n_points(ra_dec_a, 2, "ra_dec_a") if n_a is None else n_a
+    nb = (na if is_auto else _n_points(ra_dec_b, 2, "ra_dec_b")) if n_b is None else n_b
+    _slots(counts, len(e) + 1)
     _check(lib().wtheta_count(_dev_ptr(ra_dec_a), na, _dev_ptr(ra_dec_b), nb, ep, len(e) - 1,
                               1 if is_auto else 0, _dev_ptr(counts), _stream(stream)),
            "wtheta_count")
@@ -258,8 +284,9 @@ def wtheta_count_xyz(xyz_a, xyz_b, edges_deg, is_auto: bool, counts, stream=None
                      n_a: int | None = None, n_b: int | None = None):
     """xyz_*: CUDA float64 tensors, SoA (3, n) contiguous."""
     e, ep = _host_f64(edges_deg)
-    na = _n_points(xyz_a, 3) if n_a is None else n_a
-    nb = (na if is_auto else _n_points(xyz_b, 3)) if n_b is None else n_b
+    na = _n_points(xyz_a, 3, "xyz_a") if n_a is None else n_a
+    nb = (na if is_auto else _n_points(xyz_b, 3, "xyz_b")) if n_b is None else n_b
+    _slots(counts, len(e) + 1)
     _check(lib().wtheta_count_xyz(_dev_ptr(xyz_a), na, _dev_ptr(xyz_b), nb, ep, len(e) - 1,
                                   1 if is_auto else 0, _dev_ptr(counts), _stream(stream)),
            "wtheta_count_xyz")
@@ -275,8 +302,9 @@ def wtheta_shard_rows(n_a: int, n_b: int, is_auto: bool, shard: int, n_shards: i
 def wtheta_count_shard(ra_dec_a, ra_dec_b, edges_deg, is_auto: bool, shard: int, n_shards: int,
                        counts, stream=None):
     e, ep = _host_f64(edges_deg)
-    na = _n_points(ra_dec_a, 2)
-    nb = na if is_auto else _n_points(ra_dec_b, 2)
+    na = _n_points(ra_dec_a, 2, "ra_dec_a")
+    nb = na if is_auto else _n_points(ra_dec_b, 2, "ra_dec_b")
+    _slots(counts, len(e) + 1)
     _check(lib().wtheta_count_shard(_dev_ptr(ra_dec_a), na, _dev_ptr(ra_dec_b), nb, ep,
                                     len(e) - 1, 1 if is_auto else 0, shard, n_shards,
                                     _dev_ptr(counts), _stream(stream)), "wtheta_count_shard")
@@ -338,8 +366,8 @@ def wtheta_batch_plan(cats, edges_deg, tune: dict | None = None, stream=None,
     arr = (wtheta_catalog_pair * len(cats))()
     keep = []
     for i, (d, r) in enumerate(cats):
-        arr[i] = wtheta_catalog_pair(_dev_ptr(d), _n_points(d, per), _dev_ptr(r),
-                                     _n_points(r, per))
+        nd, nr = _n_points(d, per, "data %d" % i), _n_points(r, per, "rand %d" % i)
+        arr[i] = wtheta_catalog_pair(_dev_ptr(d), nd, _dev_ptr(r), nr)
         keep += [d, r]
     t = _tune_struct(tune)
     h = ctypes.c_void_p()
@@ -405,17 +433,26 @@ def wtheta_server_create(edges_deg, hbm_budget_bytes: int, max_active: int = 0,
     return Server(h, len(e) - 1)
 
 
+def _host_points(a, name):
+    """Points of a host array of interleaved RA/Dec, 1-D [ra0, dec0, ...] or
+    (n, 2): its elements over 2 (not its length, which is n for (n, 2))."""
+    if a.ndim > 2 or (a.ndim == 2 and a.shape[1] != 2) or a.size % 2:
+        raise ValueError("%s must be interleaved RA/Dec, 1-D [ra0, dec0, ...] or shape (n, 2), "
+                         "not shape %s" % (name, a.shape))
+    return a.size // 2
+
+
 def wtheta_server_submit(srv: Server, data, rand, data2=None, rand2=None) -> int:
     """Host numpy arrays of interleaved RA/Dec; auto if data2 is None, else cross."""
     arrs = [np.ascontiguousarray(x, np.float64) if x is not None else None
             for x in (data, rand, data2, rand2)]
+    n = [_host_points(x, nm) if x is not None else 0
+         for x, nm in zip(arrs, ("data", "rand", "data2", "rand2"))]
     kind = REQ_AUTO if data2 is None else REQ_CROSS
     q = wtheta_request(kind,
-                       arrs[0].ctypes.data, len(arrs[0]) // 2, arrs[1].ctypes.data, len(arrs[1]) // 2,
-                       arrs[2].ctypes.data if arrs[2] is not None else None,
-                       len(arrs[2]) // 2 if arrs[2] is not None else 0,
-                       arrs[3].ctypes.data if arrs[3] is not None else None,
-                       len(arrs[3]) // 2 if arrs[3] is not None else 0)
+                       arrs[0].ctypes.data, n[0], arrs[1].ctypes.data, n[1],
+                       arrs[2].ctypes.data if arrs[2] is not None else None, n[2],
+                       arrs[3].ctypes.data if arrs[3] is not None else None, n[3])
     rid = ctypes.c_uint64()
     _check(lib().wtheta_server_submit(srv.handle, ctypes.byref(q), ctypes.byref(rid)),
            "wtheta_server_submit")
@@ -474,8 +511,10 @@ def wtheta_count_ex(coords_a, coords_b, coords_are_xyz: bool, edges_deg, is_auto
                     tune: dict | None = None, stats=None, stream=None):
     e, ep = _host_f64(edges_deg)
     per = 3 if coords_are_xyz else 2
-    na = _n_points(coords_a, per)
-    nb = na if is_auto else _n_points(coords_b, per)
+    na = _n_points(coords_a, per, "coords_a")
+    nb = na if is_auto else _n_points(coords_b, per, "coords_b")
+    _slots(counts, len(e) + 1)
+    _slots(stats, NSTATS, "stats")
     t = _tune_struct(tune)
     _check(lib().wtheta_count_ex(_dev_ptr(coords_a), na, _dev_ptr(coords_b), nb,
                                  1 if coords_are_xyz else 0, ep, len(e) - 1, 1 if is_auto else 0,
@@ -490,8 +529,10 @@ def wtheta_count_wtheta(coords_d, coords_r, coords_are_xyz: bool, edges_deg, cou
     e, ep = _host_f64(edges_deg)
     per = 3 if coords_are_xyz else 2
     t = _tune_struct(tune)
-    _check(lib().wtheta_count_wtheta(_dev_ptr(coords_d), _n_points(coords_d, per),
-                                     _dev_ptr(coords_r), _n_points(coords_r, per),
+    nd, nr = _n_points(coords_d, per, "coords_d"), _n_points(coords_r, per, "coords_r")
+    _slots(counts, 3 * (len(e) + 1))
+    _slots(stats, NSTATS, "stats")
+    _check(lib().wtheta_count_wtheta(_dev_ptr(coords_d), nd, _dev_ptr(coords_r), nr,
                                      1 if coords_are_xyz else 0, ep, len(e) - 1, _dev_ptr(counts),
                                      ctypes.byref(t) if t is not None else None, _dev_ptr(stats),
                                      _stream(stream)), "wtheta_count_wtheta")
@@ -505,8 +546,10 @@ def wtheta_count_wtheta_shard(coords_d, coords_r, coords_are_xyz: bool, edges_de
     e, ep = _host_f64(edges_deg)
     per = 3 if coords_are_xyz else 2
     t = _tune_struct(tune)
-    _check(lib().wtheta_count_wtheta_shard(_dev_ptr(coords_d), _n_points(coords_d, per),
-                                           _dev_ptr(coords_r), _n_points(coords_r, per),
+    nd, nr = _n_points(coords_d, per, "coords_d"), _n_points(coords_r, per, "coords_r")
+    _slots(counts, 3 * (len(e) + 1))
+    _slots(stats, NSTATS, "stats")
+    _check(lib().wtheta_count_wtheta_shard(_dev_ptr(coords_d), nd, _dev_ptr(coords_r), nr,
                                            1 if coords_are_xyz else 0, ep, len(e) - 1, shard,
                                            n_shards, _dev_ptr(counts),
                                            ctypes.byref(t) if t is not None else None,
@@ -524,7 +567,9 @@ def wtheta_shard_weights(weights, shard: int, n_shards: int):
 
 
 def wtheta_radec_to_xyz(ra_dec, xyz, stream=None):
-    n = _n_points(ra_dec, 2)
+    n = _n_points(ra_dec, 2, "ra_dec")
+    _n_points(xyz, 3, "xyz")
+    _slots(xyz, 3 * n, "xyz")
     _check(lib().wtheta_radec_to_xyz(_dev_ptr(ra_dec), n, _dev_ptr(xyz), _stream(stream)),
            "wtheta_radec_to_xyz")
 
@@ -563,8 +608,9 @@ def wtheta_count_regions(coords_d, labels_d, coords_r, labels_r, edges, n_region
     e = np.ascontiguousarray(edges, np.float64)
     K = len(e) - 1
     per = 3 if coords_are_xyz else 2
-    n_d = _n_points(coords_d, per)
-    n_r = _n_points(coords_r, per)
+    n_d = _n_points(coords_d, per, "coords_d")
+    n_r = _n_points(coords_r, per, "coords_r")
+    _slots(counts, 3 * n_regions * n_regions * (K + 2))
     sizes = np.zeros(2 * n_regions, np.int64)
     _check(lib().wtheta_count_regions(_dev_ptr(coords_d), n_d, _dev_ptr(labels_d, 4, "labels_d"),
                                       _dev_ptr(coords_r), n_r, _dev_ptr(labels_r, 4, "labels_r"),
@@ -622,6 +668,7 @@ def wtheta_correlate(data, rand, edges_deg, stream=None):
     K = len(e) - 1
     counts = np.zeros(3 * (K + 2), np.uint64)
     w = np.empty(K, np.float64)
-    _check(lib().wtheta_correlate(dp, len(d) // 2, rp, len(r) // 2, ep, K, _host_u64(counts)[1],
+    _check(lib().wtheta_correlate(dp, _host_points(d, "data"), rp, _host_points(r, "rand"), ep, K,
+                                  _host_u64(counts)[1],
                                   _host_f64(w)[1], _stream(stream)), "wtheta_correlate")
     return counts.reshape(3, K + 2), w

@@ -394,3 +394,60 @@ def test_three_slot_difference_classifies_exactly(lo, hi, K, mode):
             assert np.all((d[out] > 0) == (s64[out] >= c[q])), (k, q)
             decided += int(out.sum())
     assert decided > 0
+
+
+def test_binding_refuses_misshapen_coordinates_and_short_outputs():
+    """The binding passes the library plain pointers and point counts, so it
+    checks layouts itself: unit vectors are read as SoA with stride n (a
+    row-major (n, 3) array would give wrong counts), RA/Dec as interleaved
+    pairs, and the count buffers must hold every slot the library writes.
+    Accepted layouts get as far as the device check (there is no GPU here)."""
+    torch = pytest.importorskip("torch")
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    f64 = torch.float64
+    soa = torch.zeros((3, 100), dtype=f64)
+    rd = torch.zeros(200, dtype=f64)
+    c = torch.zeros(18, dtype=torch.int64)
+    c3 = torch.zeros((3, 18), dtype=torch.int64)
+    with pytest.raises(ValueError, match=r"shape \(3, n\)"):
+        W.wtheta_count_xyz(torch.zeros((100, 3), dtype=f64), None, e, True, c)
+    with pytest.raises(ValueError, match="float64"):
+        W.wtheta_count_xyz(soa.float(), None, e, True, c)
+    with pytest.raises(ValueError, match="whole points|shape"):
+        W.wtheta_count_xyz(torch.zeros(301, dtype=f64), None, e, True, c)
+    with pytest.raises(ValueError, match="at least 18 slots"):
+        W.wtheta_count_xyz(soa, None, e, True, torch.zeros(17, dtype=torch.int64))
+    with pytest.raises(ValueError, match="interleaved RA/Dec"):
+        W.wtheta_count(torch.zeros((2, 100), dtype=f64), None, e, True, c)
+    with pytest.raises(ValueError, match="interleaved RA/Dec"):
+        W.wtheta_count(rd, torch.zeros(201, dtype=f64), e, False, c)
+    with pytest.raises(ValueError, match="at least 54 slots"):
+        W.wtheta_count_wtheta(rd, rd, False, e, c)
+    with pytest.raises(ValueError, match=r"shape \(3, n\)"):
+        W.wtheta_count_wtheta(torch.zeros((100, 3), dtype=f64), soa, True, e, c3)
+    with pytest.raises(ValueError, match="stats"):
+        W.wtheta_count_ex(rd, None, False, e, True, c, stats=torch.zeros(2, dtype=torch.int64))
+    with pytest.raises(ValueError, match="xyz"):
+        W.wtheta_radec_to_xyz(rd, torch.zeros(200, dtype=f64))
+    # the layouts the library reads are accepted: the next check is the device's
+    for call in (lambda: W.wtheta_count_xyz(soa, None, e, True, c),
+                 lambda: W.wtheta_count_xyz(soa.reshape(-1), None, e, True, c),
+                 lambda: W.wtheta_count(rd.reshape(-1, 2), None, e, True, c),
+                 lambda: W.wtheta_count_wtheta(rd, rd, False, e, c3)):
+        with pytest.raises(ValueError, match="CUDA"):
+            call()
+
+
+def test_binding_counts_host_points_by_elements():
+    """Host catalogues (wtheta_correlate, wtheta_server_submit) may be 1-D
+    interleaved RA/Dec or (n, 2): both give n points (the length of an (n, 2)
+    array is n, not 2n); other shapes are refused before any call."""
+    a = np.zeros(20)
+    assert W._host_points(a, "data") == 10
+    assert W._host_points(a.reshape(10, 2), "data") == 10
+    for bad in (np.zeros(21), np.zeros((10, 3)), np.zeros((2, 10)), np.zeros((2, 5, 2))):
+        with pytest.raises(ValueError, match="interleaved RA/Dec"):
+            W._host_points(bad, "data")
+    e = W.wtheta_edges(1.0 * ARCMIN, 5.0, 16)
+    with pytest.raises(ValueError, match="interleaved RA/Dec"):
+        W.wtheta_correlate(np.zeros((10, 3)), np.zeros(20), e)
