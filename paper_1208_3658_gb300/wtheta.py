@@ -383,6 +383,7 @@ def wtheta_batch_plan(cats, edges_deg, tune: dict | None = None, stream=None,
 
 def wtheta_batch_run(plan: BatchPlan, counts, stream=None):
     """counts: CUDA 8-byte tensor of n_cats x 3 x (K+2) slots."""
+    _slots(counts, plan.n_cats * 3 * (plan.n_bins + 2))
     _check(lib().wtheta_batch_run(plan.handle, _dev_ptr(counts), _stream(stream)),
            "wtheta_batch_run")
 
