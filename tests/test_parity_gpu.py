@@ -171,7 +171,7 @@ def test_pathological_edges_take_recheck_path(W):
     the screening table marks those buckets for FP64 recheck; still exact."""
     e = W.wtheta_edges(0.0, 180.0, 256, W.BINS_LINEAR)
     R = O.radec_to_xyz(synth.uniform(synth.FullSky(), 3000, 10, "test", "random"))
-    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    stats = torch.zeros(W.NSTATS, dtype=torch.int64, device="cuda")
     got = gpu_count_xyz(W, R, None, e, True, tune=dict(hist_mode=2), stats=stats)
     want = O.count_xyz(R, None, e, True)
     assert np.array_equal(got, want)
@@ -200,7 +200,7 @@ def test_pairs_straddling_every_edge(W):
     # single points, batched as a diagonal: count all pairs, then the
     # aligned subset via separate calls would be slow; instead check the full
     # cross count (contains all aligned pairs) and the aligned pairs alone
-    stats = torch.zeros(4, dtype=torch.int64, device="cuda")
+    stats = torch.zeros(W.NSTATS, dtype=torch.int64, device="cuda")
     got = gpu_count_xyz(W, A, B, e, False, stats=stats)
     want = O.count_xyz(A, B, e, False)
     assert np.array_equal(got, want)
@@ -349,7 +349,7 @@ def test_skipping_far_tile_pairs_is_exact(W, case):
     for a, b, auto in [(d, None, True), (d, r, False), (r, None, True)]:
         c_all = torch.zeros(len(e) + 1, dtype=torch.int64, device="cuda")
         c_skip = torch.zeros_like(c_all)
-        st = torch.zeros(4, dtype=torch.int64, device="cuda")
+        st = torch.zeros(W.NSTATS, dtype=torch.int64, device="cuda")
         W.wtheta_count_ex(a, b, False, e, auto, c_all, tune=dict(skip_far=2))
         W.wtheta_count_ex(a, b, False, e, auto, c_skip, tune=dict(skip_far=1), stats=st)
         torch.cuda.synchronize()
