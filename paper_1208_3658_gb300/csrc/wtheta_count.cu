@@ -1535,8 +1535,9 @@ __device__ __forceinline__ int round_share(int T, int m) {
 // per kind) and a ring that fills runs as one round.  When every unit is
 // taken, the jobs left in all the warps' rings are pooled and shared out
 // evenly (a warp would otherwise run its own leftovers in partial rounds
-// while the others wait at the next item's barrier); then the diagonal units
-// of an auto count that the warp took go pair by pair, with the i < j mask.
+// while the others wait at the next item's barrier; a block of one warp
+// flushes its own rings instead); then the diagonal units of an auto count
+// that the warp took go pair by pair, with the i < j mask.
 // The tile pair (I, J) stays in shared memory (sIJ) and the statistics go to
 // the block's shared counters (stat: rechecks, span pairs, skipped pairs), so
 // that the rounds run with few live registers.  Every thread of the block
